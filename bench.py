@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the split-step turbulence path on one GB300 (or N, one process per GPU).
+
+Workload: AR(1)-evolved phase screens and 8 Gaussian beams at N = 1024 (dx = 0.5 mm, L = 1 km,
+16 screens of 62.5 m, Cn^2 = 1e-15, l0 = 5 mm, L0 = 10 m, alpha = 0.99, w0 = 1.0 + 0.25 b cm).
+One step = one time step of the temporal-evolution workload: the AR update and synthesis of the
+16 screens (Eq. 4-5, S16) followed by the propagation of all 8 beams through them (Eq. 1), i.e.
+8 x 16 = 128 field-screen steps.  Metric: field-screen steps per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent realization (weak scaling, no data exchange);
+the timed region is bracketed by a barrier and synchronisation and the max over ranks is taken.
+--impl reference times the FP64 CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "field·screen steps/s at N=1024 (FP32 vs split-BF16 @ stated rel-L2), % HBM roofline"
+UNIT = "field·screen steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1024)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.15)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def algorithmic_bytes(N, B, S):
+    """Bytes one launch of each kernel kind must move (the roofline numerator), per the 2-pass model:
+    column pass: field read + write; row passes: field read + write, screen read once (shared by the
+    beams), the first pass writes only; screen synthesis: AR state read + write, column-transformed
+    spectrum write + read, screen write, PSD shape read once."""
+    px = N * N
+    col = 16 * B * px
+    row_first = 8 * B * px
+    row_mid = 16 * B * px + 4 * px
+    row_avg = (row_first + S * row_mid) / (S + 1)
+    screens = S * 36 * px + 4 * px
+    return {0: col, 1: row_avg, 2: screens}
+
+
+def load_traffic(kind_name):
+    """Per-launch DRAM bytes from the committed ncu summary, or None if the kernels changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    from paper_2604_07248_gb300 import _build
+    if data.get("csrc_sha") != _build.source_sha():
+        return None
+    k = data.get("kernels", {}).get(kind_name)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = W.config3()
+    N, S, B = wl.N, wl.S, len(wl.w0)
+    plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
+    plan.set_sources(wl.w0)
+    spec = torch.zeros((S, N, N), dtype=torch.complex64, device=dev)
+    phi = torch.zeros((S, N, N), dtype=torch.float32, device=dev)
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    real = rank  # each rank evolves its own independent realization
+    t_next = [0]
+
+    def step(src_from_field=False):
+        t = t_next[0]
+        plan.evolve_screens(spec, phi, wl.seed, t, wl.alpha, real=real, stream=stream)
+        flags = 0 if src_from_field else ts.TS_PROP_SOURCE
+        plan.propagate(U, B, phi=phi, phi_group=B, flags=flags, stream=stream)
+        t_next[0] = t + 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    launches_per_step = 2 + (1 + 2 * S)
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    clk = clocks.stop()
+
+    # per-kernel device time over a second pass of the same steps (events on the launching stream)
+    n_prof = min(args.steps, 256)
+    plan.timing(True, capacity=n_prof * (S + 1))
+    barrier()
+    for _ in range(n_prof):
+        step()
+    barrier()
+    kinds = {0: "col_pass", 1: "row_pass", 2: "screen_synthesis"}
+    kt = {k: plan.timing_read(k) for k in kinds}
+    plan.timing(False)
+    algo = algorithmic_bytes(N, B, S)
+    measured = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = float(measured["hbm_gbs"]) if measured else 6800.0
+    peak_src = "measured" if measured else "fallback"
+    per_kernel = {}
+    for k, name in kinds.items():
+        n, tot = kt[k]
+        if n == 0:
+            continue
+        avg_ms = tot / n
+        gbs = algo[k] / (avg_ms * 1e-3) / 1e9
+        per_kernel[name] = {"launches": n, "avg_us": round(avg_ms * 1e3, 3), "share": None,
+                            "algorithmic_bytes": int(algo[k]), "achieved_gbs": round(gbs, 1)}
+    total = sum(kt[k][1] for k in kinds)
+    for k, name in kinds.items():
+        if name in per_kernel:
+            per_kernel[name]["share"] = round(kt[k][1] / total, 4) if total > 0 else None
+    dom = max(per_kernel, key=lambda n: per_kernel[n]["share"] or 0)
+    dk = per_kernel[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": round(dk["achieved_gbs"] / peak, 4), "traffic": load_traffic(dom), "peak_source": peak_src,
+            "kernels": per_kernel}
+
+    # end to end through the public API with host buffers: per step, H2D of the 8 input fields from
+    # pinned memory, the screen update and propagation, D2H of the 8 receiver fields
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True)
+        host_out = torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True)
+        plan.make_sources(U, B, stream=stream)  # the 8 source fields become the host-side input
+        host_in.copy_(U)
+        n_e2e = min(args.steps, 256)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_e2e):
+            U.copy_(host_in, non_blocking=True)
+            step(src_from_field=True)
+            host_out.copy_(U, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ms_e2e = max_over_ranks(f0.elapsed_time(f1))
+        e2e = {"value": round(n_e2e * B * S * world / (ms_e2e * 1e-3), 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+               "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()), "steps": n_e2e}
+
+    value = args.steps * B * S * world / (ms * 1e-3)
+    res = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "N": N, "dx": wl.dx, "L": wl.L, "screens": S, "beams": B,
+                   "cn2": wl.cn2[0], "alpha": wl.alpha, "field_screen_steps_per_step": B * S,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "working set 256 MiB (AR spectra 128 + screens 64 + fields 64) > 126 MB L2; no flush"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        res["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args.cpu_seconds)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle as it stands, single-threaded
+# ------------------------------------------------------------------------------------------------
+def oracle_unit_times(budget_s: float):
+    """Time the oracle on a bounded sample of the workload: AR updates + syntheses of a few screens
+    and the propagation of one beam through a few steps, both at N = 1024."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2604_07248_gb300 import workloads as W
+
+    wl = W.config3()
+    md = O.medium(W.LAMBDA, wl.N, wl.dx, l0=W.L0_INNER, L0=W.L0_OUTER)
+    dz, cn2 = wl.dz[0], wl.cn2[0]
+    # screens: t = 0 spectrum, then AR steps with synthesis
+    t0 = time.perf_counter()
+    spec, _ = O.screen_spectrum(md, cn2, dz, 0, wl.seed, 0, 0, 0)
+    n_scr = 0
+    ph = []
+    while True:
+        spec, _ = O.ar_step(md, cn2, dz, 0, wl.seed, 0, 0, n_scr + 1, wl.alpha, spec)
+        ph.append(O.screen_from_spectrum(md, spec))
+        n_scr += 1
+        if time.perf_counter() - t0 > budget_s * 0.4 or n_scr >= 16:
+            break
+    t_screen = (time.perf_counter() - t0) / n_scr
+    U = O.source_gaussian(wl.N, wl.dx, wl.w0[0])
+    t1 = time.perf_counter()
+    n_prop = 0
+    while True:
+        U = O.propagate(md, [dz], ph[n_prop % len(ph)][None], U)
+        n_prop += 1
+        if time.perf_counter() - t1 > budget_s * 0.6 or n_prop >= 128:
+            break
+    t_prop = (time.perf_counter() - t1) / n_prop
+    return t_screen, t_prop, n_scr, n_prop
+
+
+def cpu_baseline(budget_s: float):
+    from paper_2604_07248_gb300 import workloads as W
+
+    wl = W.config3()
+    S, B = wl.S, len(wl.w0)
+    t_screen, t_prop, n_scr, n_prop = oracle_unit_times(budget_s)
+    t_step = S * t_screen + B * S * t_prop
+    return {"value": round(B * S / t_step, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle, N=1024: {n_scr} screen AR updates+syntheses ({t_screen:.3f} s each) and "
+                       f"{n_prop} single-beam propagation steps ({t_prop:.3f} s each), scaled to one time step "
+                       f"(16 screens + 128 field-screen steps)")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2604_07248_gb300 import workloads as W
+
+    wl = W.config3()
+    S, B = wl.S, len(wl.w0)
+    budget_total = 150.0
+    per_step_budget = max(0.5, budget_total / max(1, args.steps + args.warmup))
+    for _ in range(min(args.warmup, 1)):
+        oracle_unit_times(min(per_step_budget, 2.0))
+    rates = []
+    t0 = time.perf_counter()
+    steps_done = 0
+    for _ in range(args.steps):
+        ts_, tp, _, _ = oracle_unit_times(per_step_budget)
+        rates.append(B * S / (S * ts_ + B * S * tp))
+        steps_done += 1
+        if time.perf_counter() - t0 > budget_total:
+            break
+    value = statistics.median(rates)
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "steps_timed": steps_done, "warmup": args.warmup,
+           "ms_per_step": round(B * S / value * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "N": wl.N, "screens": S, "beams": B},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "per step: FP64 oracle screen AR updates and single-beam propagation steps "
+                                      "at N=1024, scaled to one time step"},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * turbscreen.h -- C ABI of the GB300 (sm_103a) split-step optical-turbulence library.
+ *
+ * The library computes the data-parallel hot path of the split-step method of TurPy
+ * (Greene et al., arXiv 2604.07248): FFT phase screens from a von Karman phase PSD with 3-level
+ * subharmonics (Sec. 2.1-2.2, Eq. 2-3, App. B-C), AR(1) temporal evolution of the screens in the
+ * Fourier domain (Sec. 2.3, Eq. 4-5), the propagate/modulate loop of Eq. 1 with the angular-spectrum
+ * transfer function (Sec. 2.4), its adjoint, per-pixel intensity moments (S25) and the two-mask
+ * dual-domain D2NN receiver (Sec. 2.5, 4.1).  Every step runs in hand-written CUDA kernels.
+ *
+ * Conventions used throughout:
+ *   - complex fields are interleaved complex64 (float re, float im), row-major [N][N]
+ *     (row j = y index, column i = x index); batches are [B][N][N], contiguous.
+ *   - x = (i - N/2) dx for sources and apertures (beam centred on pixel (N/2, N/2)); screens use
+ *     the DFT origin x = i dx.
+ *   - spectral index f(n) = n for n < N/2, else n - N; kappa = 2 pi f / (N dx).
+ *   - gradients follow the convention g = dL/dRe + i dL/dIm, so a linear map P back-propagates as P^H.
+ *   - all device pointers are owned by the caller; a plan owns only its own tables and workspace
+ *     (allocated once in ts_plan_create).  No call other than ts_plan_create / ts_plan_destroy
+ *     allocates or frees device memory.
+ *   - all work is enqueued asynchronously on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Argument checks happen on the host before any launch;
+ *     a failing check launches nothing.  One plan must not be used concurrently from two streams
+ *     (it owns a single workspace).
+ *   - on error a call returns a non-zero ts_status and ts_last_error() gives a one-line detail.
+ */
+#ifndef TURBSCREEN_H
+#define TURBSCREEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TS_OK = 0,
+    TS_ERR_INVALID_ARG = 1,    /* a pointer, size or parameter is out of range                   */
+    TS_ERR_ALIASING = 2,       /* a step dz exceeds the angular-spectrum aliasing limit (Eq. 7)   */
+    TS_ERR_WORKSPACE = 3,      /* the plan's workspace cannot hold the request (batch too large)  */
+    TS_ERR_CUDA = 4,           /* a CUDA runtime call failed (detail in ts_last_error())          */
+    TS_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up                              */
+    TS_ERR_UNSUPPORTED = 6     /* a grid size or regime this build does not implement             */
+} ts_status;
+
+/* Medium (Fig. 1A inputs): vacuum wavelength [m], mean refractive index n0, inner scale l0 [m]
+ * (<= 0: no inner-scale roll-off), outer scale L0 [m] (<= 0 or inf: no outer scale).
+ * The refractive-index PSD is the modified von Karman form (S17 written through Cn^2, S18):
+ *   Phi_n = 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6) exp(-kappa^2 / kappa_m^2),
+ *   kappa0 = 2 pi / L0, kappa_m = 2 pi / l0, and a screen covering dz has Phi_phi = 2 pi k^2 dz Phi_n (S14). */
+typedef struct {
+    double lambda;
+    double n0;
+    double l0;
+    double L0;
+} ts_medium;
+
+/* Grid: N x N points (N in {128, 256, 512, 1024, 2048}), spacing dx [m]. */
+typedef struct {
+    int N;
+    double dx;
+} ts_grid;
+
+/* Path (Fig. 1A "range samples" and "turbulence strength over path"): n_screens intervals; interval
+ * s has length dz[s] [m] and structure constant cn2[s] [m^-2/3].  Both arrays are HOST pointers read
+ * during ts_plan_create only.  Step s of Eq. 1 propagates dz[s] and then applies screen s. */
+typedef struct {
+    int n_screens;
+    const double* dz;
+    const double* cn2;
+} ts_path;
+
+typedef struct ts_plan_s* ts_plan;
+
+/* ts_plan_create flags */
+#define TS_PLAN_ALLOW_ALIASING 1 /* skip the Eq. 7 step-size check (caller accepts aliasing) */
+
+/* Creates a plan for one medium, grid and path.  sh_levels is 0 or 3 (subharmonic levels, Eq. 2,
+ * scale factor 3).  max_batch bounds the number of fields per ts_propagate / ts_propagate_backward
+ * call and the number of realizations per ts_make_screens chunk.  The plan builds its FP64-derived
+ * tables on the current CUDA device (twiddles, per-step transfer-function factors, PSD shape,
+ * subharmonic basis) and allocates its workspace there; the call synchronises the device.
+ * Errors: TS_ERR_INVALID_ARG (null pointers, N not supported, dx/lambda/dz <= 0, cn2 < 0,
+ * sh_levels not 0/3, max_batch < 1), TS_ERR_ALIASING (some dz above the Eq. 7 limit
+ * dz_max = (N dx / 2) sqrt(k^2 - kappa_max^2) / kappa_max with kappa_max = pi / dx, unless
+ * TS_PLAN_ALLOW_ALIASING), TS_ERR_UNSUPPORTED (grid reaches the evanescent region), TS_ERR_CUDA. */
+ts_status ts_plan_create(ts_plan* plan, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
+                         int sh_levels, int max_batch, int flags);
+
+/* Frees the plan's device memory (synchronises the device).  NULL is accepted. */
+ts_status ts_plan_destroy(ts_plan plan);
+
+/* Device bytes held by the plan (tables + workspace). */
+size_t ts_plan_device_bytes(ts_plan plan);
+
+/* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
+ * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */
+double ts_max_step(const ts_medium* medium, const ts_grid* grid);
+
+/* Source table used by ts_propagate with TS_PROP_SOURCE: field b starts as source (b mod n).
+ * w0[k] > 0: collimated Gaussian exp(-r^2 / w0^2) centred on pixel (N/2, N/2) (S22);
+ * w0[k] <= 0: unit plane wave (Sec. 3.3).  w0 is a HOST array of n entries (n <= 64). */
+ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0);
+
+/* Source fields (S22; plane wave of Sec. 3.3): writes the plan's source table into field
+ * (device complex64 [B][N][N]), field b = source (b mod n).  Requires ts_plan_set_sources. */
+ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream);
+
+/* Independent screens (Sec. 2.1, Fig. 1B-C; S16; Eq. 2-3): for realization r in
+ * [real_base, real_base + n_real) and screen s in [0, S):
+ *   phi = Re(sum_kappa s(kappa) c(kappa) exp(+i kappa.x)) + phi_SH - mean,
+ * s(kappa) = sqrt(Phi_phi(kappa)) dkappa with s(0) = 0, c = Philox4x32-10 complex Gaussian noise.
+ * phi: device float32 [n_real][S][N][N], written.  Counter layout of the noise:
+ * key = (seed mod 2^32, seed >> 32), counter = (word0, s, r, (purpose << 24) | t) with t = 0;
+ * grid bins (m, n) and (m + N/2, n) share word0 = m N + n (m < N/2); subharmonic cell q of level p
+ * uses purpose 1 and word0 = (p - 1) 8 + q / 2. */
+ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* stream);
+
+/* AR(1) evolution of the S screens of realization `real` (Sec. 2.3, Eq. 4-5):
+ *   t == 0: spec = s(kappa) c^(0)                                   (stationary start)
+ *   t >= 1: spec = alpha exp(i theta) spec + sqrt(1 - alpha^2) s(kappa) c^(t),
+ *           theta = -2 pi T (f_x vx + f_y vy)  (wind translation; T = 0 disables it),
+ * then phi = Re(IDFT_unnormalised(spec)) + phi_SH - mean.  The subharmonic coefficients evolve
+ * by the same rule with their own frequencies.
+ * spec: device complex64 [S][N][N], read (t >= 1) and written.  sh_state: device complex128
+ * [S][27] when the plan has subharmonics (else NULL), read/written likewise.  phi: device float32
+ * [S][N][N], written.  0 <= alpha <= 1. */
+ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t t, double alpha, double vx,
+                            double vy, double T, void* spec, void* sh_state, float* phi, void* stream);
+
+/* ts_propagate flags */
+#define TS_PROP_SOURCE 1    /* start from the plan's source table instead of reading `field`     */
+#define TS_PROP_INTENSITY 2 /* write I = |U|^2 (float32 [B][N][N]) to `intensity`               */
+#define TS_PROP_NO_FIELD 4  /* do not store the output field (only meaningful with INTENSITY)   */
+
+/* Split-step propagation, Eq. 1, for s = 0..S-1:  U <- IFFT2(FFT2(U) H_s) exp(i phi_s), with
+ *   H_s = exp(-i dz_s kappa^2 / (k + sqrt(k^2 - kappa^2)))  (H_as of Sec. 2.4 without its global
+ *   piston exp(i k dz_s)), FFT2 unnormalised, IFFT2 with 1/N^2.
+ * field: device complex64 [B][N][N], input (unless TS_PROP_SOURCE) and output.
+ * phi: device float32 screens [G][S][N][N] with G = ceil(B / phi_group): field b uses screen set
+ * b / phi_group.  phi == NULL regenerates the screens from (seed, real_base + b / phi_group)
+ * exactly as ts_make_screens does (plan workspace; no allocation).
+ * intensity: device float32 [B][N][N] (TS_PROP_INTENSITY) else NULL.
+ * beam_sums: device float64 [B][2] or NULL: per field sum I and sum r^2 I (r from pixel (N/2, N/2)).
+ * Errors: TS_ERR_INVALID_ARG, TS_ERR_WORKSPACE (B > max_batch), TS_ERR_CUDA. */
+ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int phi_group, int flags, uint64_t seed,
+                       uint32_t real_base, float* intensity, double* beam_sums, void* stream);
+
+/* Adjoint of ts_propagate with respect to the input field: grad <- P^H grad, i.e. for s = S-1..0
+ *   g <- g exp(-i phi_s);  g <- IFFT2(FFT2(g) conj(H_s)).
+ * grad: device complex64 [B][N][N] in/out (dL/dU_out in, dL/dU_in out).  phi as in ts_propagate;
+ * NULL regenerates each screen from its seed (bit-identical to the forward screens) one step at a
+ * time in the plan workspace instead of storing them. */
+ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, int phi_group, uint64_t seed,
+                                uint32_t real_base, void* stream);
+
+/* Per-pixel intensity moments across realizations (S25 with Welford's algorithm, Sec. 3.3).
+ * intensity: device float32 [B][N][N]; fields b with b mod n_groups == g form the chunk of group g
+ * (B / n_groups fields each, B divisible by n_groups).  mean, m2: device float64 [n_groups][N][N]
+ * holding `count` realizations per group before the call; the chunk is merged with the pairwise
+ * (Chan et al.) update, so results do not depend on how realizations are split into calls.
+ * After the call each group holds count + B / n_groups realizations. */
+ts_status ts_moments_accumulate(ts_plan plan, const float* intensity, int B, int n_groups, int64_t count,
+                                double* mean, double* m2, void* stream);
+
+/* Scintillation index map SI = (m2 / count) / mean^2 (S25, population variance), its plane
+ * average and the on-axis value (pixel (N/2, N/2)), for n_groups groups.  si_map: device float64
+ * [n_groups][N][N] or NULL; si_mean, si_center: device float64 [n_groups] or NULL. */
+ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2, int n_groups, int64_t count,
+                              double* si_map, double* si_mean, double* si_center, void* stream);
+
+/* Two-mask dual-domain D2NN receiver (Sec. 2.5, 4.1), batch of B fields U (device complex64):
+ *   Z1 = exp(i th1) A U;  W2 = exp(i th2) C(Z1);  V = C^-1(W2);  I = |V|^2,
+ * C = fftshift o FFT2 o ifftshift / N (lens as a unitary centred DFT), A = disk of diameter
+ * `aperture` [m] centred on pixel (N/2, N/2).  Loss against the reference intensity Iref
+ * (device float32 [N][N]): kind 0 = mean |I - Iref| (MAE, Sec. 2.5), kind 1 = mean (I - Iref)^2,
+ * mean over batch and pixels; written to loss (device float64 [1]).
+ * th1, th2: device float32 [N][N].  ws: device complex64 workspace [3][B][N][N] kept for the
+ * backward call (Z1, W2, V). */
+ts_status ts_d2nn_forward(ts_plan plan, const void* U, int B, const float* th1, const float* th2, double aperture,
+                          const float* Iref, int kind, void* ws, float* intensity, double* loss, void* stream);
+
+/* Adjoint of ts_d2nn_forward: writes dL/dth1, dL/dth2 (device float32 [N][N], sums over the
+ * batch) and dL/dU (device complex64 [B][N][N]) from the workspace of the forward call:
+ *   g_V = 2 V dL/dI; g_W2 = C(g_V); dL/dth2 = sum Im(g_W2 conj W2); g_Z1 = C^-1(exp(-i th2) g_W2);
+ *   dL/dth1 = sum Im(g_Z1 conj Z1); dL/dU = A exp(-i th1) g_Z1. */
+ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* th2, double aperture,
+                           const float* Iref, int kind, const void* ws, const float* intensity, float* g_th1,
+                           float* g_th2, void* gU, void* stream);
+
+/* Kernel timing for roofline measurements.  While enabled, the plan records a CUDA event pair on
+ * the launching stream around every launch of: kind 0 = propagation column pass, kind 1 =
+ * propagation row pass, kind 2 = screen synthesis (column + row pass of one ts_make_screens /
+ * ts_evolve_screens / regeneration call).  `capacity` event pairs are created per kind (no device
+ * memory); launches beyond it are not timed.  Enabling resets the counters.
+ * ts_plan_timing_read waits for the recorded events and returns the number of timed launches of
+ * `kind` and their summed device time in milliseconds. */
+ts_status ts_plan_timing(ts_plan plan, int enable, int capacity);
+ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* total_ms);
+
+/* Raw Philox4x32-10 words (Salmon et al., SC'11) of n counters, for bit-exact checks of the noise
+ * generator used by the screens: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key).  ctr and out
+ * are device uint32 arrays of 4n words. */
+ts_status ts_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out, void* stream);
+
+const char* ts_status_string(ts_status status);
+
+/* One-line detail of the last error raised on the calling host thread ("" if none). */
+const char* ts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TURBSCREEN_H */

@@ -1,0 +1,218 @@
+"""ctypes binding of libturbscreen.so (include/turbscreen.h).
+
+Argument marshalling only: every function below forwards device pointers, sizes and the CUDA
+stream handle to the C ABI, which runs every step of the path in the library's CUDA kernels.
+There is no CPU path: if the library cannot be built or loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+TS_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "aliasing (Eq. 7)", 3: "workspace", 4: "CUDA error",
+          5: "device timeout", 6: "unsupported"}
+
+TS_PLAN_ALLOW_ALIASING = 1
+TS_PROP_SOURCE = 1
+TS_PROP_INTENSITY = 2
+TS_PROP_NO_FIELD = 4
+
+
+class TsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class Medium(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("n0", C.c_double), ("l0", C.c_double), ("L0", C.c_double)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("N", C.c_int), ("dx", C.c_double)]
+
+
+class Path(C.Structure):
+    _fields_ = [("n_screens", C.c_int), ("dz", C.POINTER(C.c_double)), ("cn2", C.POINTER(C.c_double))]
+
+
+# name -> (restype, argtypes); mirrors include/turbscreen.h
+_P, _I, _D, _U32, _U64, _I64 = C.c_void_p, C.c_int, C.c_double, C.c_uint32, C.c_uint64, C.c_int64
+SIGNATURES = {
+    "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
+    "ts_plan_destroy": (_I, [_P]),
+    "ts_plan_device_bytes": (C.c_size_t, [_P]),
+    "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
+    "ts_plan_set_sources": (_I, [_P, _I, _P]),
+    "ts_make_sources": (_I, [_P, _P, _I, _P]),
+    "ts_make_screens": (_I, [_P, _U64, _U32, _I, _P, _P]),
+    "ts_evolve_screens": (_I, [_P, _U64, _U32, _U32, _D, _D, _D, _D, _P, _P, _P, _P]),
+    "ts_propagate": (_I, [_P, _P, _I, _P, _I, _I, _U64, _U32, _P, _P, _P]),
+    "ts_propagate_backward": (_I, [_P, _P, _I, _P, _I, _U64, _U32, _P]),
+    "ts_moments_accumulate": (_I, [_P, _P, _I, _I, _I64, _P, _P, _P]),
+    "ts_moments_finalize": (_I, [_P, _P, _P, _I, _I64, _P, _P, _P, _P]),
+    "ts_d2nn_forward": (_I, [_P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
+    "ts_d2nn_backward": (_I, [_P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "ts_philox4x32_10": (_I, [_P, _U32, _U32, _I, _P, _P]),
+    "ts_plan_timing": (_I, [_P, _I, _I]),
+    "ts_plan_timing_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "ts_status_string": (C.c_char_p, [_I]),
+    "ts_last_error": (C.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libturbscreen.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libturbscreen.so not found at {path}; run __graft_entry__.build()")
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != TS_OK:
+        detail = load().ts_last_error().decode()
+        raise TsError(status, where, detail)
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a tensor (or None)."""
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def max_step(lam, N, dx, n0=1.0) -> float:
+    """Eq. 7 aliasing-limited step [m] for this wavelength and grid."""
+    return load().ts_max_step(C.byref(Medium(lam, n0, 0.0, 0.0)), C.byref(Grid(N, dx)))
+
+
+def philox4x32_10(ctr, key0, key1, out, stream=None):
+    """Philox4x32-10 words of n counters (ctr, out: device uint32 tensors of 4n words)."""
+    n = ctr.numel() // 4
+    _check(load().ts_philox4x32_10(_ptr(ctr), int(key0), int(key1), n, _ptr(out), _stream(stream)),
+           "ts_philox4x32_10")
+
+
+class Plan:
+    """One medium + grid + path on the current CUDA device (ts_plan)."""
+
+    def __init__(self, lam, N, dx, dz, cn2, n0=1.0, l0=0.0, L0=0.0, sh_levels=0, max_batch=1, flags=0):
+        lib = load()
+        dz = [float(x) for x in dz]
+        cn2 = [float(x) for x in cn2]
+        if len(dz) != len(cn2):
+            raise ValueError("dz and cn2 need one entry per screen")
+        self.N, self.dx, self.S, self.lam = int(N), float(dx), len(dz), float(lam)
+        self.dz, self.cn2 = dz, cn2
+        self.sh_levels, self.max_batch = int(sh_levels), int(max_batch)
+        L0v = float(L0) if (L0 is not None and math.isfinite(L0)) else 0.0
+        med = Medium(float(lam), float(n0), float(l0), L0v)
+        grid = Grid(int(N), float(dx))
+        dza = (C.c_double * len(dz))(*dz)
+        cna = (C.c_double * len(cn2))(*cn2)
+        path = Path(len(dz), dza, cna)
+        h = C.c_void_p()
+        _check(lib.ts_plan_create(C.byref(h), C.byref(med), C.byref(grid), C.byref(path), int(sh_levels),
+                                  int(max_batch), int(flags)), "ts_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        return load().ts_plan_device_bytes(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ts_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def timing(self, enable: bool, capacity: int = 0):
+        """Record CUDA events around each launch (kinds: 0 column pass, 1 row pass, 2 screens)."""
+        _check(load().ts_plan_timing(self._h, 1 if enable else 0, int(capacity)), "ts_plan_timing")
+
+    def timing_read(self, kind: int):
+        """(number of timed launches, summed device milliseconds) for one kernel kind."""
+        n, ms = C.c_int(), C.c_double()
+        _check(load().ts_plan_timing_read(self._h, int(kind), C.byref(n), C.byref(ms)), "ts_plan_timing_read")
+        return n.value, ms.value
+
+    def set_sources(self, w0):
+        w = (C.c_double * len(w0))(*[float(x) for x in w0])
+        _check(load().ts_plan_set_sources(self._h, len(w0), w), "ts_plan_set_sources")
+
+    def make_sources(self, field, B, stream=None):
+        _check(load().ts_make_sources(self._h, _ptr(field), int(B), _stream(stream)), "ts_make_sources")
+
+    def make_screens(self, phi, seed, real_base=0, n_real=1, stream=None):
+        _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _stream(stream)),
+               "ts_make_screens")
+
+    def evolve_screens(self, spec, phi, seed, t, alpha, real=0, vx=0.0, vy=0.0, T=0.0, sh_state=None, stream=None):
+        _check(load().ts_evolve_screens(self._h, int(seed), int(real), int(t), float(alpha), float(vx), float(vy),
+                                        float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _stream(stream)),
+               "ts_evolve_screens")
+
+    def propagate(self, field, B, phi=None, phi_group=1, flags=0, seed=0, real_base=0, intensity=None,
+                  beam_sums=None, stream=None):
+        _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), int(phi_group), int(flags), int(seed),
+                                   int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream)),
+               "ts_propagate")
+
+    def propagate_backward(self, grad, B, phi=None, phi_group=1, seed=0, real_base=0, stream=None):
+        _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), int(phi_group), int(seed),
+                                            int(real_base), _stream(stream)), "ts_propagate_backward")
+
+    def moments_accumulate(self, intensity, B, n_groups, count, mean, m2, stream=None):
+        _check(load().ts_moments_accumulate(self._h, _ptr(intensity), int(B), int(n_groups), int(count), _ptr(mean),
+                                            _ptr(m2), _stream(stream)), "ts_moments_accumulate")
+
+    def moments_finalize(self, mean, m2, n_groups, count, si_map=None, si_mean=None, si_center=None, stream=None):
+        _check(load().ts_moments_finalize(self._h, _ptr(mean), _ptr(m2), int(n_groups), int(count), _ptr(si_map),
+                                          _ptr(si_mean), _ptr(si_center), _stream(stream)), "ts_moments_finalize")
+
+    def d2nn_forward(self, U, B, th1, th2, aperture, Iref, kind, ws, intensity, loss, stream=None):
+        _check(load().ts_d2nn_forward(self._h, _ptr(U), int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref),
+                                      int(kind), _ptr(ws), _ptr(intensity), _ptr(loss), _stream(stream)),
+               "ts_d2nn_forward")
+
+    def d2nn_backward(self, B, th1, th2, aperture, Iref, kind, ws, intensity, g_th1, g_th2, gU, stream=None):
+        _check(load().ts_d2nn_backward(self._h, int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref), int(kind),
+                                       _ptr(ws), _ptr(intensity), _ptr(g_th1), _ptr(g_th2), _ptr(gU),
+                                       _stream(stream)), "ts_d2nn_backward")

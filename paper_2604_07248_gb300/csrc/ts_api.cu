@@ -1,0 +1,513 @@
+// ts_api.cu -- the C ABI (include/turbscreen.h): argument checks, plan construction and the
+// launch sequences of the split-step path.  Every numeric step runs in the library's kernels; the
+// host computes only per-plan scalars (amplitudes, limits) in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ts_internal.h"
+
+namespace ts {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ts_status cuda_check(cudaError_t e, const char* where)
+{
+    if (e == cudaSuccess) return TS_OK;
+    set_error(std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return TS_ERR_CUDA;
+}
+
+namespace {
+
+ts_status fail(ts_status st, const std::string& msg)
+{
+    set_error(msg);
+    return st;
+}
+
+bool supported_N(int N) { return N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048; }
+
+double wavenumber(const ts_medium* m) { return 2.0 * M_PI * m->n0 / m->lambda; }
+
+// Phi_phi(kappa) = 2 pi k^2 dz 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6) exp(-kappa^2 / kappa_m^2)   (S14, S17)
+double phase_psd(const Plan& p, double cn2, double dz, double k2)
+{
+    const double k0sq = (p.L0 > 0.0 && std::isfinite(p.L0)) ? std::pow(2.0 * M_PI / p.L0, 2.0) : 0.0;
+    const double roll = p.l0 > 0.0 ? std::exp(-k2 / std::pow(2.0 * M_PI / p.l0, 2.0)) : 1.0;
+    return 2.0 * M_PI * p.k * p.k * dz * 0.033 * cn2 * std::pow(k2 + k0sq, -11.0 / 6.0) * roll;
+}
+
+template <class T>
+cudaError_t dalloc(Plan& p, T** ptr, size_t count)
+{
+    const size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e == cudaSuccess) p.bytes += bytes;
+    return e;
+}
+
+void destroy_events(Plan* p)
+{
+    for (auto& v : p->ev) {
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+        v.clear();
+    }
+    for (int& u : p->ev_used) u = 0;
+}
+
+// Runs `launch` between two recorded events when timing is on and events remain for `kind`.
+template <class F>
+cudaError_t timed(Plan& p, int kind, cudaStream_t st, F&& launch)
+{
+    const int u = p.ev_used[kind];
+    const bool on = p.timing && 2 * (u + 1) <= (int)p.ev[kind].size();
+    if (on) cudaEventRecord(p.ev[kind][2 * u], st);
+    cudaError_t e = launch();
+    if (on) {
+        cudaEventRecord(p.ev[kind][2 * u + 1], st);
+        p.ev_used[kind] = u + 1;
+    }
+    return e;
+}
+
+void free_plan(Plan* p)
+{
+    destroy_events(p);
+    void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
+                    p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// regenerate screen `s` of the G screen sets (realizations real_base .. real_base + G - 1) into ws_phi
+ts_status regen_screen(Plan& p, uint64_t seed, uint32_t real_base, int G, int s, cudaStream_t st)
+{
+    ScreenArgs a{};
+    a.seed = seed;
+    a.s_begin = s;
+    a.s_count = 1;
+    a.r_begin = real_base;
+    a.items = G;
+    a.t = 0;
+    a.phi = p.ws_phi;
+    return cuda_check(timed(p, 2, st, [&] { return launch_screens(p, SC_INDEP, a, st); }), "screen synthesis");
+}
+
+}  // namespace
+}  // namespace ts
+
+using namespace ts;
+
+extern "C" {
+
+const char* ts_status_string(ts_status s)
+{
+    switch (s) {
+    case TS_OK: return "ok";
+    case TS_ERR_INVALID_ARG: return "invalid argument";
+    case TS_ERR_ALIASING: return "step exceeds the angular-spectrum aliasing limit (Eq. 7)";
+    case TS_ERR_WORKSPACE: return "request exceeds the plan workspace";
+    case TS_ERR_CUDA: return "CUDA error";
+    case TS_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case TS_ERR_UNSUPPORTED: return "unsupported size or regime";
+    }
+    return "unknown status";
+}
+
+const char* ts_last_error(void) { return g_last_error.c_str(); }
+
+double ts_max_step(const ts_medium* m, const ts_grid* g)
+{
+    if (!m || !g || g->N <= 0 || !(g->dx > 0.0) || !(m->lambda > 0.0) || !(m->n0 > 0.0)) return -1.0;
+    const double k = wavenumber(m);
+    const double kmax = M_PI / g->dx;
+    if (kmax >= k) return 0.0;
+    return 0.5 * g->N * g->dx * std::sqrt(k * k - kmax * kmax) / kmax;
+}
+
+ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
+                         int sh_levels, int max_batch, int flags)
+{
+    set_error("");
+    if (!out || !medium || !grid || !path) return fail(TS_ERR_INVALID_ARG, "null pointer argument");
+    *out = nullptr;
+    if (!supported_N(grid->N)) return fail(TS_ERR_INVALID_ARG, "N must be one of 128, 256, 512, 1024, 2048");
+    if (!(grid->dx > 0.0) || !(medium->lambda > 0.0) || !(medium->n0 > 0.0))
+        return fail(TS_ERR_INVALID_ARG, "dx, lambda and n0 must be positive");
+    if (path->n_screens < 1 || path->n_screens > kMaxScreens || !path->dz || !path->cn2)
+        return fail(TS_ERR_INVALID_ARG, "path needs 1..64 screens with dz and cn2 arrays");
+    if (sh_levels != 0 && sh_levels != 3) return fail(TS_ERR_INVALID_ARG, "sh_levels must be 0 or 3");
+    if (max_batch < 1) return fail(TS_ERR_INVALID_ARG, "max_batch must be >= 1");
+
+    Plan tmp;
+    tmp.N = grid->N;
+    tmp.dx = grid->dx;
+    tmp.S = path->n_screens;
+    tmp.sh_levels = sh_levels;
+    tmp.max_batch = max_batch;
+    tmp.lambda = medium->lambda;
+    tmp.n0 = medium->n0;
+    tmp.l0 = medium->l0;
+    tmp.L0 = medium->L0;
+    tmp.k = wavenumber(medium);
+    tmp.dk = 2.0 * M_PI / (grid->N * grid->dx);
+    const double dzmax = ts_max_step(medium, grid);
+    const double kap2max = 2.0 * std::pow(M_PI / grid->dx, 2.0);
+    for (int s = 0; s < tmp.S; ++s) {
+        const double dz = path->dz[s], cn2 = path->cn2[s];
+        if (!(dz > 0.0) || !(cn2 >= 0.0) || !std::isfinite(dz) || !std::isfinite(cn2))
+            return fail(TS_ERR_INVALID_ARG, "dz must be > 0 and cn2 >= 0");
+        if (!(flags & TS_PLAN_ALLOW_ALIASING) && dz > dzmax) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "step %d: dz = %g m exceeds the Eq. 7 limit %g m", s, dz, dzmax);
+            return fail(TS_ERR_ALIASING, buf);
+        }
+        if (kap2max >= tmp.k * tmp.k) return fail(TS_ERR_UNSUPPORTED, "grid reaches the evanescent region");
+        const double root = std::sqrt(tmp.k * tmp.k - kap2max);
+        const double delta = dz * kap2max * kap2max / (2.0 * tmp.k * (tmp.k + root) * (tmp.k + root));
+        if (delta > 0.25)
+            return fail(TS_ERR_UNSUPPORTED, "non-paraxial phase correction above 0.25 rad at the grid corner");
+        tmp.dz[s] = dz;
+        tmp.cn2[s] = cn2;
+    }
+
+    Plan* p = new Plan(tmp);
+    cudaError_t e = cudaGetDevice(&p->device);
+    const int N = p->N, S = p->S;
+    const size_t N2 = (size_t)N * N;
+    // screens per synthesis launch: whole screen sets, about 256 MiB of complex workspace
+    const int budget = (int)((256ull << 20) / (8 * N2));
+    const int sets = std::max(1, std::min(max_batch, budget / S));
+    p->screen_chunk = std::max(S * sets, std::min(max_batch, std::max(1, budget)));
+    p->screen_chunk = ((p->screen_chunk + S - 1) / S) * S;
+    auto ok = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    ok(dalloc(*p, &p->tw, N));
+    ok(dalloc(*p, &p->P, (size_t)S * N));
+    ok(dalloc(*p, &p->amp, S));
+    ok(dalloc(*p, &p->g, N2));
+    ok(dalloc(*p, &p->tilt, 2 * (size_t)N));
+    if (sh_levels) {
+        ok(dalloc(*p, &p->shx, 3 * (size_t)N));
+        ok(dalloc(*p, &p->shy, 3 * (size_t)N));
+        ok(dalloc(*p, &p->shy_mean, 3));
+        ok(dalloc(*p, &p->shb, (size_t)S * kShCoef));
+        ok(dalloc(*p, &p->ws_shv, (size_t)p->screen_chunk * kShVectors * N));
+        ok(dalloc(*p, &p->ws_shmean, p->screen_chunk));
+        ok(dalloc(*p, &p->ws_sha, (size_t)p->screen_chunk * kShCoef));
+    }
+    ok(dalloc(*p, &p->ws_y, (size_t)p->screen_chunk * N2));
+    ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * N2));
+    ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
+    if (e != cudaSuccess) {
+        ts_status st = cuda_check(e, "ts_plan_create allocation");
+        free_plan(p);
+        return st;
+    }
+    // per-screen amplitudes: s(kappa) = amp_s g(kappa), amp_s = sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
+    float amp[kMaxScreens];
+    for (int s = 0; s < S; ++s) amp[s] = (float)(std::sqrt(2.0 * M_PI * p->k * p->k * p->dz[s] * 0.033 * p->cn2[s]) * p->dk);
+    ok(cudaMemcpy(p->amp, amp, sizeof(float) * S, cudaMemcpyHostToDevice));
+    if (sh_levels) {
+        // b[p][q] = sqrt(Phi_phi(kappa_pq)) dkappa / 3^p, kappa_pq = (n', m') dkappa / 3^p   (Eq. 2)
+        double shb[kMaxScreens * kShCoef];
+        for (int s = 0; s < S; ++s)
+            for (int lv = 1; lv <= 3; ++lv) {
+                const double dkp = p->dk / std::pow(3.0, lv);
+                for (int q = 0; q < 9; ++q) {
+                    const int mp = q / 3 - 1, np = q % 3 - 1;
+                    const double k2 = (np * dkp) * (np * dkp) + (mp * dkp) * (mp * dkp);
+                    shb[s * kShCoef + (lv - 1) * 9 + q] = (q == 4) ? 0.0 : std::sqrt(phase_psd(*p, p->cn2[s], p->dz[s], k2)) * dkp;
+                }
+            }
+        ok(cudaMemcpy(p->shb, shb, sizeof(double) * S * kShCoef, cudaMemcpyHostToDevice));
+    }
+    ok(build_tables(*p));
+    ok(prepare_prop_kernels(N));
+    ok(prepare_screen_kernels(N));
+    if (e != cudaSuccess) {
+        ts_status st = cuda_check(e, "ts_plan_create tables");
+        free_plan(p);
+        return st;
+    }
+    *out = reinterpret_cast<ts_plan>(p);
+    return TS_OK;
+}
+
+ts_status ts_plan_destroy(ts_plan plan)
+{
+    if (!plan) return TS_OK;
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(p);
+    return cuda_check(e, "ts_plan_destroy");
+}
+
+size_t ts_plan_device_bytes(ts_plan plan) { return plan ? reinterpret_cast<Plan*>(plan)->bytes : 0; }
+
+ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0)
+{
+    if (!plan || !w0 || n < 1 || n > kMaxSources) return fail(TS_ERR_INVALID_ARG, "need a plan and 1..64 source waists");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    for (int i = 0; i < n; ++i) p->src_coef[i] = w0[i] > 0.0 ? (float)(p->dx * p->dx / (w0[i] * w0[i])) : -1.0f;
+    p->n_src = n;
+    return TS_OK;
+}
+
+ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream)
+{
+    if (!plan || !field || B < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_sources: need plan, field and B >= 1");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (p->n_src < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_sources: no source table set");
+    RowArgs ra{};
+    ra.field = reinterpret_cast<float2*>(field);
+    ra.phi_group = 1;
+    ra.B = B;
+    return cuda_check(launch_row_pass(*p, RP_IN_SOURCE | RP_STORE, ra, as_stream(stream)), "ts_make_sources");
+}
+
+ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* stream)
+{
+    if (!plan || !phi || n_real < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_screens: need plan, phi and n_real >= 1");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    ScreenArgs a{};
+    a.seed = seed;
+    a.s_begin = 0;
+    a.s_count = p->S;
+    a.r_begin = real_base;
+    a.items = n_real * p->S;
+    a.t = 0;
+    a.phi = phi;
+    cudaStream_t st = as_stream(stream);
+    return cuda_check(timed(*p, 2, st, [&] { return launch_screens(*p, SC_INDEP, a, st); }), "ts_make_screens");
+}
+
+ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t t, double alpha, double vx, double vy,
+                            double T, void* spec, void* sh_state, float* phi, void* stream)
+{
+    if (!plan || !spec || !phi) return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: need plan, spec and phi");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (p->sh_levels && !sh_state) return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: plan has subharmonics, sh_state needed");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(TS_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
+    if (t > 0xFFFFFFu) return fail(TS_ERR_INVALID_ARG, "t must be below 2^24");
+    cudaStream_t st = as_stream(stream);
+    ScreenArgs a{};
+    a.seed = seed;
+    a.s_begin = 0;
+    a.s_count = p->S;
+    a.r_begin = real;
+    a.items = p->S;
+    a.t = t;
+    a.alpha_d = alpha;
+    a.beta_d = std::sqrt(1.0 - alpha * alpha);
+    a.alpha = (float)a.alpha_d;
+    a.beta = (float)a.beta_d;
+    a.spec = reinterpret_cast<float2*>(spec);
+    a.sh_state = reinterpret_cast<double2*>(sh_state);
+    a.phi = phi;
+    a.tilt = (t > 0) && T != 0.0 && (vx != 0.0 || vy != 0.0);
+    a.vx = vx;
+    a.vy = vy;
+    a.T = T;
+    if (a.tilt) {
+        ts_status s0 = cuda_check(build_tilt(*p, vx, vy, T, st), "ts_evolve_screens tilt");
+        if (s0 != TS_OK) return s0;
+    }
+    return cuda_check(timed(*p, 2, st, [&] { return launch_screens(*p, t == 0 ? SC_AR_INIT : SC_AR_STEP, a, st); }),
+                      "ts_evolve_screens");
+}
+
+ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int phi_group, int flags, uint64_t seed,
+                       uint32_t real_base, float* intensity, double* beam_sums, void* stream)
+{
+    if (!plan || !field) return fail(TS_ERR_INVALID_ARG, "ts_propagate: need plan and field");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (B < 1 || phi_group < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate: B and phi_group must be >= 1");
+    if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_propagate: B exceeds the plan's max_batch");
+    if ((flags & TS_PROP_SOURCE) && p->n_src < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate: no source table set");
+    if ((flags & TS_PROP_INTENSITY) && !intensity) return fail(TS_ERR_INVALID_ARG, "ts_propagate: intensity buffer needed");
+    if (beam_sums && !(flags & TS_PROP_INTENSITY))
+        return fail(TS_ERR_INVALID_ARG, "ts_propagate: beam_sums need TS_PROP_INTENSITY");
+    if ((flags & TS_PROP_NO_FIELD) && !(flags & TS_PROP_INTENSITY))
+        return fail(TS_ERR_INVALID_ARG, "ts_propagate: TS_PROP_NO_FIELD needs TS_PROP_INTENSITY");
+    cudaStream_t st = as_stream(stream);
+    const int N = p->N, S = p->S;
+    const size_t N2 = (size_t)N * N;
+    const int G = (B + phi_group - 1) / phi_group;
+    float2* U = reinterpret_cast<float2*>(field);
+
+    RowArgs ra{};
+    ra.field = U;
+    ra.phi_group = phi_group;
+    ra.phase_sign = 1.0f;
+    ra.B = B;
+    ra.phi = nullptr;
+    const int f0 = ((flags & TS_PROP_SOURCE) ? RP_IN_SOURCE : 0) | RP_OUT_FREQ | RP_STORE;
+    ts_status stt =
+        cuda_check(timed(*p, 1, st, [&] { return launch_row_pass(*p, f0, ra, st); }), "ts_propagate first row pass");
+    if (stt != TS_OK) return stt;
+    for (int s = 0; s < S; ++s) {
+        stt = cuda_check(timed(*p, 0, st, [&] { return launch_col_pass(*p, s, false, U, B, st); }),
+                         "ts_propagate column pass");
+        if (stt != TS_OK) return stt;
+        if (phi) {
+            ra.phi = phi + (size_t)s * N2;
+            ra.phi_set_stride = (long long)S * N2;
+        } else {
+            if ((stt = regen_screen(*p, seed, real_base, G, s, st)) != TS_OK) return stt;
+            ra.phi = p->ws_phi;
+            ra.phi_set_stride = (long long)N2;
+        }
+        int rf = RP_IN_FREQ | RP_PHASE | RP_STORE;
+        if (s < S - 1) {
+            rf |= RP_OUT_FREQ;
+        } else if (flags & TS_PROP_INTENSITY) {
+            rf |= RP_INTENSITY;
+            if (flags & TS_PROP_NO_FIELD) rf &= ~RP_STORE;
+            ra.intensity = intensity;
+            ra.rows = beam_sums ? p->ws_rows : nullptr;
+        }
+        stt = cuda_check(timed(*p, 1, st, [&] { return launch_row_pass(*p, rf, ra, st); }), "ts_propagate row pass");
+        if (stt != TS_OK) return stt;
+    }
+    if (beam_sums) return cuda_check(launch_row_sums(*p, p->ws_rows, B, beam_sums, st), "ts_propagate beam sums");
+    return TS_OK;
+}
+
+ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, int phi_group, uint64_t seed,
+                                uint32_t real_base, void* stream)
+{
+    if (!plan || !grad) return fail(TS_ERR_INVALID_ARG, "ts_propagate_backward: need plan and grad");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (B < 1 || phi_group < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate_backward: B and phi_group must be >= 1");
+    if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_propagate_backward: B exceeds the plan's max_batch");
+    cudaStream_t st = as_stream(stream);
+    const int N = p->N, S = p->S;
+    const size_t N2 = (size_t)N * N;
+    const int G = (B + phi_group - 1) / phi_group;
+    float2* g = reinterpret_cast<float2*>(grad);
+    RowArgs ra{};
+    ra.field = g;
+    ra.phi_group = phi_group;
+    ra.phase_sign = -1.0f;
+    ra.B = B;
+    ts_status stt = TS_OK;
+    auto set_screen = [&](int s) -> ts_status {
+        if (phi) {
+            ra.phi = phi + (size_t)s * N2;
+            ra.phi_set_stride = (long long)S * N2;
+            return TS_OK;
+        }
+        ra.phi = p->ws_phi;
+        ra.phi_set_stride = (long long)N2;
+        return regen_screen(*p, seed, real_base, G, s, st);
+    };
+    if ((stt = set_screen(S - 1)) != TS_OK) return stt;
+    stt = cuda_check(launch_row_pass(*p, RP_PHASE | RP_OUT_FREQ | RP_STORE, ra, st), "backward first row pass");
+    if (stt != TS_OK) return stt;
+    for (int s = S - 1; s >= 0; --s) {
+        stt = cuda_check(launch_col_pass(*p, s, true, g, B, st), "backward column pass");
+        if (stt != TS_OK) return stt;
+        if (s > 0) {
+            if ((stt = set_screen(s - 1)) != TS_OK) return stt;
+            stt = cuda_check(launch_row_pass(*p, RP_IN_FREQ | RP_PHASE | RP_OUT_FREQ | RP_STORE, ra, st),
+                             "backward row pass");
+        } else {
+            ra.phi = nullptr;
+            stt = cuda_check(launch_row_pass(*p, RP_IN_FREQ | RP_STORE, ra, st), "backward last row pass");
+        }
+        if (stt != TS_OK) return stt;
+    }
+    return TS_OK;
+}
+
+ts_status ts_moments_accumulate(ts_plan plan, const float* intensity, int B, int n_groups, int64_t count, double* mean,
+                                double* m2, void* stream)
+{
+    if (!plan || !intensity || !mean || !m2) return fail(TS_ERR_INVALID_ARG, "ts_moments_accumulate: null pointer");
+    if (n_groups < 1 || B < n_groups || B % n_groups != 0 || count < 0)
+        return fail(TS_ERR_INVALID_ARG, "ts_moments_accumulate: B must be a positive multiple of n_groups");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    return cuda_check(launch_moments(*p, intensity, B, n_groups, count, mean, m2, as_stream(stream)),
+                      "ts_moments_accumulate");
+}
+
+ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2, int n_groups, int64_t count,
+                              double* si_map, double* si_mean, double* si_center, void* stream)
+{
+    if (!plan || !mean || !m2 || n_groups < 1 || count < 1)
+        return fail(TS_ERR_INVALID_ARG, "ts_moments_finalize: need moments with count >= 1");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    return cuda_check(launch_moments_finalize(*p, mean, m2, n_groups, count, si_map, si_mean, si_center, as_stream(stream)),
+                      "ts_moments_finalize");
+}
+
+ts_status ts_plan_timing(ts_plan plan, int enable, int capacity)
+{
+    if (!plan || capacity < 0) return fail(TS_ERR_INVALID_ARG, "ts_plan_timing: need a plan and capacity >= 0");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    destroy_events(p);
+    p->timing = enable != 0;
+    if (!p->timing) return TS_OK;
+    for (auto& v : p->ev) {
+        v.resize(2 * (size_t)capacity);
+        for (auto& e : v) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) {
+                e = nullptr;
+                p->timing = false;
+                return cuda_check(err, "ts_plan_timing");
+            }
+        }
+    }
+    return TS_OK;
+}
+
+ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* total_ms)
+{
+    if (!plan || kind < 0 || kind > 2 || !launches || !total_ms)
+        return fail(TS_ERR_INVALID_ARG, "ts_plan_timing_read: bad arguments");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    double tot = 0.0;
+    for (int i = 0; i < p->ev_used[kind]; ++i) {
+        cudaError_t e = cudaEventSynchronize(p->ev[kind][2 * i + 1]);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev[kind][2 * i], p->ev[kind][2 * i + 1]);
+        if (e != cudaSuccess) return cuda_check(e, "ts_plan_timing_read");
+        tot += ms;
+    }
+    *launches = p->ev_used[kind];
+    *total_ms = tot;
+    return TS_OK;
+}
+
+ts_status ts_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out, void* stream)
+{
+    if (!ctr || !out || n < 1) return fail(TS_ERR_INVALID_ARG, "ts_philox4x32_10: need ctr, out and n >= 1");
+    return cuda_check(launch_philox(ctr, key0, key1, n, out, as_stream(stream)), "ts_philox4x32_10");
+}
+
+ts_status ts_d2nn_forward(ts_plan, const void*, int, const float*, const float*, double, const float*, int, void*, float*,
+                          double*, void*)
+{
+    return fail(TS_ERR_UNSUPPORTED, "ts_d2nn_forward: not available in this build");
+}
+
+ts_status ts_d2nn_backward(ts_plan, int, const float*, const float*, double, const float*, int, const void*,
+                           const float*, float*, float*, void*, void*)
+{
+    return fail(TS_ERR_UNSUPPORTED, "ts_d2nn_backward: not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// ts_device.cuh -- device building blocks for the split-step turbulence kernels (sm_103a).
+//
+//  * complex64 arithmetic on float2
+//  * Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
+//  * fully unrolled in-register DFTs of radix 2..32 with compile-time twiddles
+//  * a Stockham autosort line FFT: each thread keeps E points of a length-N line in registers,
+//    stages of radix <= E exchange through padded shared memory (Govindaraju et al. formulation:
+//    stage with sub-length Ns reads x[j + r N/R], twiddles by W_{Ns R}^{(j mod Ns) r}, writes
+//    y[(j/Ns) Ns R + (j mod Ns) + r Ns]).  The last stage leaves output point t + i T in register i
+//    of thread t, the same placement the first stage reads, so transforms chain without an
+//    exchange.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ts {
+
+// ----------------------------------------------------------------------------------------------
+// complex helpers
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// ----------------------------------------------------------------------------------------------
+// Philox4x32-10 and Box-Muller.  Counter layout (shared definition with the host documentation):
+//   key = (seed mod 2^32, seed >> 32), ctr = (word0, screen, realization, (purpose << 24) | t).
+// ----------------------------------------------------------------------------------------------
+struct u32x4 {
+    uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 ctr, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * ctr.a, hi0 = __umulhi(0xD2511F53u, ctr.a);
+        const uint32_t lo1 = 0xCD9E8D57u * ctr.c, hi1 = __umulhi(0xCD9E8D57u, ctr.c);
+        ctr = u32x4{hi1 ^ ctr.b ^ k0, lo1, hi0 ^ ctr.d ^ k1, lo0};
+    }
+    return ctr;
+}
+
+// ((w >> 8) + 0.5) * 2^-24, exact in binary32
+__device__ __forceinline__ float u01f(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+
+// Box-Muller: radius sqrt(-2 ln ua), angle 2 pi ub (sincospif keeps the angle exact).
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb)
+{
+    const float rad = sqrtf(-2.0f * logf(u01f(wa)));
+    float s, c;
+    sincospif(2.0f * u01f(wb), &s, &c);
+    return make_float2(rad * c, rad * s);
+}
+
+__device__ __forceinline__ double u01d(uint32_t w) { return ((double)(w >> 8) + 0.5) * 5.9604644775390625e-8; }
+
+__device__ __forceinline__ double2 box_muller_d(uint32_t wa, uint32_t wb)
+{
+    const double rad = sqrt(-2.0 * log(u01d(wa)));
+    double s, c;
+    sincospi(2.0 * u01d(wb), &s, &c);
+    return make_double2(rad * c, rad * s);
+}
+
+// ----------------------------------------------------------------------------------------------
+// compile-time twiddles exp(SIGN 2 pi i k / 32) from the first octant of cos(2 pi k / 32)
+// ----------------------------------------------------------------------------------------------
+struct Oct {
+    static constexpr double c[9] = {1.0,
+                                    0.98078528040323043,
+                                    0.92387953251128674,
+                                    0.83146961230254524,
+                                    0.70710678118654757,
+                                    0.55557023301960229,
+                                    0.38268343236508984,
+                                    0.19509032201612833,
+                                    0.0};
+};
+constexpr double cos32(int k)
+{
+    k &= 31;
+    return k <= 8 ? Oct::c[k] : k <= 16 ? -Oct::c[16 - k] : k <= 24 ? -Oct::c[k - 16] : Oct::c[32 - k];
+}
+constexpr double sin32(int k)
+{
+    k &= 31;
+    return k <= 8 ? Oct::c[8 - k] : k <= 16 ? Oct::c[k - 8] : k <= 24 ? -Oct::c[24 - k] : -Oct::c[k - 24];
+}
+
+// v * exp(SIGN 2 pi i K / R), with the trivial factors done without multiplications
+template <int R, int K, int SIGN>
+__device__ __forceinline__ float2 twiddle_const(float2 v)
+{
+    constexpr int k32 = (K * 32 / R) & 31;
+    if constexpr (k32 == 0) {
+        return v;
+    } else if constexpr (k32 == 8) {  // SIGN * i
+        return SIGN > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    } else if constexpr (k32 == 16) {
+        return make_float2(-v.x, -v.y);
+    } else if constexpr (k32 == 24) {  // -SIGN * i
+        return SIGN > 0 ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+    } else {
+        constexpr float c = (float)cos32(k32);
+        constexpr float s = (float)(SIGN * sin32(k32));
+        return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+    }
+}
+
+// In-register DFT of length R on a compact array x[0..R-1] (natural order in and out),
+// X[k] = sum_n x[n] exp(SIGN 2 pi i n k / R).  Recursive radix-2 decimation in time; every index
+// is a compile-time constant after unrolling, so x stays in registers.
+template <int R, int SIGN>
+struct Dft {
+    __device__ __forceinline__ static void run(float2* x)
+    {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int n = 0; n < R / 2; ++n) {
+            e[n] = x[2 * n];
+            o[n] = x[2 * n + 1];
+        }
+        Dft<R / 2, SIGN>::run(e);
+        Dft<R / 2, SIGN>::run(o);
+        combine<0>(x, e, o);
+    }
+    template <int K>
+    __device__ __forceinline__ static void combine(float2* x, const float2* e, const float2* o)
+    {
+        if constexpr (K < R / 2) {
+            const float2 t = twiddle_const<R, K, SIGN>(o[K]);
+            x[K] = cadd(e[K], t);
+            x[K + R / 2] = csub(e[K], t);
+            combine<K + 1>(x, e, o);
+        }
+    }
+};
+
+template <int SIGN>
+struct Dft<2, SIGN> {
+    __device__ __forceinline__ static void run(float2* x)
+    {
+        const float2 a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    }
+};
+
+template <int SIGN>
+struct Dft<1, SIGN> {
+    __device__ __forceinline__ static void run(float2*) {}
+};
+
+// Strided wrapper: transforms v[0], v[S], ..., v[(R-1) S].
+template <int R, int SIGN, int S>
+__device__ __forceinline__ void dft_strided(float2* v)
+{
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[r * S];
+    Dft<R, SIGN>::run(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r * S] = x[r];
+}
+
+// ----------------------------------------------------------------------------------------------
+// Stockham line FFT configuration per N.  E points per thread, T = N / E threads per line.
+// Stage k has sub-length Ns_k = E^k and radix R_k = min(E, N / Ns_k).
+// ----------------------------------------------------------------------------------------------
+template <int N>
+struct FftCfg {
+    static constexpr int E = (N <= 256) ? 16 : 32;
+    static constexpr int T = N / E;
+    static constexpr int stages = (N <= E) ? 1 : (N <= E * E ? 2 : 3);
+    static constexpr int Ns(int k) { return k == 0 ? 1 : (k == 1 ? E : E * E); }
+    static constexpr int Rk(int k) { return (N / Ns(k)) < E ? (N / Ns(k)) : E; }
+    // offset of stage k's twiddles in the per-N table (stage 0 has none): sum (R_k' - 1) Ns_k'
+    static constexpr int tw_off(int k) { return k <= 1 ? 0 : (Rk(1) - 1) * Ns(1) + (k <= 2 ? 0 : (Rk(2) - 1) * Ns(2)); }
+    static constexpr int tw_size = tw_off(stages);
+    // padded index inside one line's exchange buffer (in float2 units)
+    __host__ __device__ static constexpr int pad(int x) { return x + x / E; }
+    static constexpr int padded = N + N / E;
+};
+
+// One Stockham stage.  v[i] holds point t + i T on entry (stage input ordering).  Non-final
+// stages write to the line buffer `buf` (padded) and read back the next stage's inputs; `bar`
+// synchronises all threads sharing the buffer.
+template <int N, int K, int SIGN, class Bar>
+__device__ __forceinline__ void fft_stage(float2 (&v)[FftCfg<N>::E], float2* buf, int t, const float2* __restrict__ tw,
+                                          Bar bar)
+{
+    using C = FftCfg<N>;
+    constexpr int E = C::E, T = C::T;
+    constexpr int R = C::Rk(K), Ns = C::Ns(K), B = E / R;
+    constexpr bool LAST = (K == C::stages - 1);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = t + q * T;
+        if constexpr (K > 0) {
+            const int jm = j & (Ns - 1);
+            const float2* w = tw + C::tw_off(K) + jm;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 wr = __ldg(w + (r - 1) * Ns);
+                v[q + r * B] = SIGN < 0 ? cmul(v[q + r * B], wr) : cmulc(v[q + r * B], wr);
+            }
+        }
+        dft_strided<R, SIGN, B>(v + q);
+    }
+    if constexpr (!LAST) {
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int j = t + q * T;
+            const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[C::pad(base + r * Ns)] = v[q + r * B];
+        }
+        bar();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = buf[C::pad(t + i * T)];
+        bar();
+    }
+}
+
+// Full length-N transform of one line: X[k] = sum_n x[n] exp(SIGN 2 pi i n k / N), unnormalised.
+template <int N, int SIGN, class Bar>
+__device__ __forceinline__ void line_fft(float2 (&v)[FftCfg<N>::E], float2* buf, int t, const float2* __restrict__ tw,
+                                         Bar bar)
+{
+    using C = FftCfg<N>;
+    fft_stage<N, 0, SIGN>(v, buf, t, tw, bar);
+    if constexpr (C::stages > 1) fft_stage<N, 1, SIGN>(v, buf, t, tw, bar);
+    if constexpr (C::stages > 2) fft_stage<N, 2, SIGN>(v, buf, t, tw, bar);
+}
+
+struct WarpBar {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockBar {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// spectral index map f(n) = n for n < N/2, else n - N
+__device__ __forceinline__ int kidx(int n, int N) { return n < (N >> 1) ? n : n - N; }
+
+}  // namespace ts

@@ -1,0 +1,118 @@
+// ts_internal.h -- plan layout and kernel launchers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/turbscreen.h"
+
+namespace ts {
+
+constexpr int kMaxScreens = 64;
+constexpr int kMaxSources = 64;
+constexpr int kShCoef = 27;     // 3 levels x 9 sub-grid cells (cell 4 = DC, unused)
+constexpr int kShVectors = 7;   // V0, (Vc_p, Vs_p) for p = 1..3
+
+struct Plan {
+    int device = 0;
+    int N = 0;
+    int S = 0;
+    int sh_levels = 0;
+    int max_batch = 0;
+    int screen_chunk = 0;  // screens per synthesis launch (workspace rows)
+    double lambda = 0, n0 = 1, l0 = 0, L0 = 0, dx = 0, k = 0, dk = 0;
+    double dz[kMaxScreens] = {};
+    double cn2[kMaxScreens] = {};
+    int n_src = 0;
+    float src_coef[kMaxSources] = {};  // dx^2 / w0^2, or -1 for a plane wave
+
+    // device tables (FP64-built, FP32-stored unless noted)
+    float2* tw = nullptr;      // Stockham stage twiddles, forward sign
+    float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N
+    float* dcoef = nullptr;    // [S] dz / (2 k^3)  (non-paraxial phase correction)
+    float* amp = nullptr;      // [S] sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
+    float* g = nullptr;        // [N][N] (kappa^2 + kappa0^2)^(-11/12) exp(-kappa^2 / 2 kappa_m^2), g(0) = 0
+    double2* shx = nullptr;    // [3][N] exp(i dkappa_p x_i), FP64
+    float2* shy = nullptr;     // [3][N] (cos, sin)(dkappa_p y_j)
+    double2* shy_mean = nullptr;  // [3] mean_j (cos, sin)(dkappa_p y_j), FP64
+    double* shb = nullptr;     // [S][27] subharmonic amplitudes sqrt(Phi_phi) dkappa_p, FP64
+    float2* tilt = nullptr;    // [2][N] AR translation factors (x then y), rebuilt per call
+
+    // workspace
+    float2* ws_y = nullptr;       // [screen_chunk][N][N] column-transformed screen spectra
+    float* ws_shv = nullptr;      // [screen_chunk][7][N] subharmonic row vectors
+    float* ws_shmean = nullptr;   // [screen_chunk] subharmonic piston
+    double2* ws_sha = nullptr;    // [screen_chunk][27] subharmonic coefficients
+    float* ws_phi = nullptr;      // [max_batch][N][N] regenerated screens (phi == NULL paths)
+    double* ws_rows = nullptr;    // [max_batch][N][2] per-row beam sums
+    size_t bytes = 0;
+
+    // optional per-kernel-kind event timing (kinds: 0 column pass, 1 row pass, 2 screen synthesis)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev[3];
+    int ev_used[3] = {0, 0, 0};
+};
+
+// error plumbing
+void set_error(const std::string& msg);
+ts_status cuda_check(cudaError_t e, const char* where);
+
+// ---- launchers (N dispatch inside) ----
+// tables
+cudaError_t build_tables(Plan& p);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int n, uint32_t* out, cudaStream_t st);
+cudaError_t build_tilt(Plan& p, double vx, double vy, double T, cudaStream_t st);
+
+// propagation passes
+enum RowFlags : int {
+    RP_IN_SOURCE = 1,
+    RP_IN_FREQ = 2,
+    RP_PHASE = 4,
+    RP_OUT_FREQ = 8,
+    RP_INTENSITY = 16,
+    RP_STORE = 32,
+};
+struct RowArgs {
+    float2* field;
+    const float* phi;          // screen s of set 0 (or nullptr)
+    long long phi_set_stride;  // elements between screen sets
+    int phi_group;
+    float phase_sign;
+    const float* src_coef;     // device copy not needed: passed by value below
+    float* intensity;
+    double* rows;              // [B][N][2]
+    int B;
+};
+cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStream_t st);
+cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st);
+cudaError_t prepare_prop_kernels(int N);
+cudaError_t prepare_screen_kernels(int N);
+cudaError_t launch_row_sums(const Plan& p, const double* rows, int B, double* out, cudaStream_t st);
+
+// screens
+enum ScreenMode : int { SC_INDEP = 0, SC_AR_INIT = 1, SC_AR_STEP = 2 };
+struct ScreenArgs {
+    uint64_t seed;
+    int s_begin, s_count;      // screens s_begin .. s_begin + s_count - 1
+    uint32_t r_begin;          // realizations r_begin + z / s_count
+    int items;                 // s_count * realizations
+    uint32_t t;                // AR step (noise tag)
+    float alpha, beta;         // AR weights
+    double alpha_d, beta_d;
+    float2* spec;              // AR state [items][N][N]
+    double2* sh_state;         // AR subharmonic state [items][27]
+    float* phi;                // output [items][N][N]
+    bool tilt;
+    double vx, vy, T;
+};
+cudaError_t launch_screens(Plan& p, int mode, const ScreenArgs& a, cudaStream_t st);
+
+// moments
+cudaError_t launch_moments(const Plan& p, const float* I, int B, int G, int64_t count, double* mean, double* m2,
+                           cudaStream_t st);
+cudaError_t launch_moments_finalize(const Plan& p, const double* mean, const double* m2, int G, int64_t count,
+                                    double* si_map, double* si_mean, double* si_center, cudaStream_t st);
+
+}  // namespace ts

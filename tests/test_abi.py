@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/turbscreen.h declares; host-side
+argument checks reject bad input before any CUDA call (CPU only, no kernel launches)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_07248_gb300 import binding as bd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "turbscreen.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ts_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = declared_functions()
+    for required in ("ts_plan_create", "ts_plan_destroy", "ts_make_screens", "ts_evolve_screens", "ts_propagate",
+                     "ts_propagate_backward", "ts_moments_accumulate", "ts_moments_finalize", "ts_d2nn_forward",
+                     "ts_d2nn_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = bd.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    # and the binding mirrors every declaration
+    assert set(declared_functions()) <= set(bd.SIGNATURES)
+
+
+def test_max_step_is_eq7_reading():
+    # dz_max = (N dx / 2) sqrt(k^2 - kmax^2) / kmax, kmax = pi / dx  (approximately N dx^2 / lambda)
+    for lam, N, dx in [(1.55e-6, 128, 2e-3), (1.55e-6, 1024, 5e-4), (1.064e-6, 1024, 3.4e-4)]:
+        k = 2 * np.pi / lam
+        kmax = np.pi / dx
+        expect = 0.5 * N * dx * np.sqrt(k * k - kmax * kmax) / kmax
+        assert abs(bd.max_step(lam, N, dx) - expect) < 1e-9 * expect
+        assert abs(bd.max_step(lam, N, dx) / (N * dx * dx / lam) - 1) < 1e-3
+    assert abs(bd.max_step(1.55e-6, 1024, 5e-4) - 165.1) < 0.2
+    assert abs(bd.max_step(1.55e-6, 128, 2e-3) - 330.2) < 0.2
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=100), 1),
+    (dict(N=96), 1),
+    (dict(dx=0.0), 1),
+    (dict(lam=-1.0), 1),
+    (dict(dz=[-5.0], cn2=[1e-15]), 1),
+    (dict(dz=[10.0], cn2=[-1e-15]), 1),
+    (dict(sh_levels=2), 1),
+    (dict(max_batch=0), 1),
+    (dict(dz=[1000.0], cn2=[1e-15]), 2),  # above the Eq. 7 limit of 330 m at N = 128, dx = 2 mm
+])
+def test_plan_rejects_bad_arguments_before_touching_the_gpu(kw, status):
+    args = dict(lam=1.55e-6, N=128, dx=2e-3, dz=[200.0], cn2=[1e-15], sh_levels=0, max_batch=1)
+    args.update(kw)
+    with pytest.raises(bd.TsError) as ei:
+        bd.Plan(args["lam"], args["N"], args["dx"], args["dz"], args["cn2"], sh_levels=args["sh_levels"],
+                max_batch=args["max_batch"])
+    assert ei.value.status == status
+
+
+def test_status_strings_and_null_handling():
+    lib = bd.load()
+    for s in range(7):
+        assert lib.ts_status_string(s)
+    assert lib.ts_plan_destroy(None) == 0
+    assert lib.ts_plan_device_bytes(None) == 0
+    assert lib.ts_make_screens(None, 0, 0, 1, None, None) == 1
+    assert lib.ts_propagate(None, None, 1, None, 1, 0, 0, 0, None, None, None) == 1
+    assert b"need" in lib.ts_last_error()

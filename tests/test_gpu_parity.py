@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeds.
+
+Tolerance (FP32 paths): relative L2 error <= 1e-5 per field / screen, as the method's accuracy
+target states; integer work (Philox words) is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker keeps these off CPU runs
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2604_07248_gb300 as ts  # noqa: E402
+
+LAM = 1.55e-6
+DEV = torch.device("cuda:0")
+TOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) else np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cfield(B, N):
+    return torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+
+
+def omedium(N, dx, l0=5e-3, L0=10.0):
+    return O.medium(LAM, N, dx, l0=l0, L0=L0)
+
+
+# ------------------------------------------------------------------------------------------------
+def test_philox_words_bit_exact():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key = (0xA4093822, 0x299F31D0)
+    out = torch.zeros(4096 * 4, dtype=torch.int32, device=DEV)
+    ts.philox4x32_10(torch.from_numpy(ctr.view(np.int32).ravel()).to(DEV), key[0], key[1], out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(4096, 4)
+    for i in range(0, 4096, 97):
+        assert np.array_equal(got[i], O.philox4x32_10(ctr[i], key))
+    # published known answer (zero counter, zero key)
+    z = torch.zeros(4, dtype=torch.int32, device=DEV)
+    ts.philox4x32_10(z, 0, 0, out[:4])
+    torch.cuda.synchronize()
+    assert [int(x) for x in out[:4].cpu().numpy().view(np.uint32)] == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+@pytest.mark.parametrize("N,dx,sh,n_real,S", [(128, 2e-3, 0, 2, 5), (256, 1e-3, 3, 2, 3), (512, 1e-3, 3, 1, 2)])
+def test_screens_match_oracle(N, dx, sh, n_real, S):
+    dz, cn2 = [200.0] * S, [10 ** -13.5] * S
+    plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, sh_levels=sh, max_batch=n_real)
+    phi = torch.zeros((n_real, S, N, N), dtype=torch.float32, device=DEV)
+    seed = 0x2604072480 + 2
+    plan.make_screens(phi, seed, real_base=7, n_real=n_real)
+    torch.cuda.synchronize()
+    got = phi.cpu().numpy()
+    md = omedium(N, dx)
+    for r in range(n_real):
+        for s in range(S):
+            ref = O.make_screen(md, cn2[s], dz[s], sh, seed, s, 7 + r)
+            assert rel_l2(got[r, s], ref) < TOL, (r, s, rel_l2(got[r, s], ref))
+            assert abs(got[r, s].astype(np.float64).mean()) < 1e-5 * np.abs(ref).max()
+
+
+def test_screen_chunks_with_ragged_tail():
+    # 3 realizations x 16 screens at N = 1024: the 256 MiB synthesis workspace holds 32 screens, so
+    # the launch loop runs one full chunk and one ragged chunk of 16.
+    N, S = 1024, 16
+    plan = ts.Plan(LAM, N, 5e-4, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=3)
+    phi = torch.zeros((3, S, N, N), dtype=torch.float32, device=DEV)
+    plan.make_screens(phi, 11, real_base=0, n_real=3)
+    torch.cuda.synchronize()
+    md = omedium(N, 5e-4)
+    for (r, s) in [(0, 0), (1, 15), (2, 0), (2, 15)]:
+        ref = O.make_screen(md, 1e-15, 62.5, 0, 11, s, r)
+        assert rel_l2(phi[r, s].cpu().numpy(), ref) < TOL
+
+
+def test_config1_path_matches_oracle_and_vacuum_matches_analytic():
+    # 128-point grid, dx = 2 mm, L = 1 km in 5 steps, Cn^2 = 1e-15, l0 = 5 mm, L0 = 10 m, w0 = 2 cm
+    N, dx, S, w0 = 128, 2e-3, 5, 0.02
+    seed = 0x2604072480 + 1
+    for cn2 in (1e-15, 0.0):
+        plan = ts.Plan(LAM, N, dx, [200.0] * S, [cn2] * S, l0=5e-3, L0=10.0, max_batch=1)
+        plan.set_sources([w0])
+        U = cfield(1, N)
+        plan.propagate(U, 1, phi=None, flags=ts.TS_PROP_SOURCE, seed=seed, real_base=0)
+        torch.cuda.synchronize()
+        got = U[0].cpu().numpy()
+        md = omedium(N, dx)
+        phis = None if cn2 == 0 else np.stack([O.make_screen(md, cn2, 200.0, 0, seed, s, 0) for s in range(S)])
+        ref = O.propagate(md, [200.0] * S, phis, O.source_gaussian(N, dx, w0))
+        assert rel_l2(got, ref) < TOL, rel_l2(got, ref)
+    # vacuum: analytic paraxial beam, W(1 km) = 3.176 cm
+    zR = np.pi * w0 ** 2 / LAM
+    W = w0 * np.sqrt(1 + (1000 / zR) ** 2)
+    R = 1000 * (1 + (zR / 1000) ** 2)
+    x = (np.arange(N) - N // 2) * dx
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    ana = (w0 / W) * np.exp(-r2 / W ** 2 + 1j * 2 * np.pi / LAM * r2 / (2 * R) - 1j * np.arctan(1000 / zR))
+    assert rel_l2(got, ana) < 2e-6
+
+
+def test_propagate_with_given_screens_and_batches():
+    # oracle screens fed as float32, input fields read from memory, B = 3 with 2 screen sets
+    N, dx, S = 256, 1e-3, 4
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [150.0, 100.0, 120.0, 130.0], [1e-14, 3e-15, 1e-14, 2e-14], l0=5e-3, L0=10.0,
+                   max_batch=3)
+    phis = np.stack([np.stack([O.make_screen(md, 1e-14, 150.0, 0, 3, s, r) for s in range(S)]) for r in range(2)])
+    rng = np.random.default_rng(4)
+    U0 = [O.source_gaussian(N, dx, 0.02 + 0.01 * b) * np.exp(1j * rng.normal(0, 0.1, (N, N))) for b in range(3)]
+    U = torch.from_numpy(np.stack(U0).astype(np.complex64)).to(DEV)
+    phi_t = torch.from_numpy(phis.astype(np.float32)).to(DEV)
+    plan.propagate(U, 3, phi=phi_t, phi_group=2)
+    torch.cuda.synchronize()
+    got = U.cpu().numpy()
+    for b in range(3):
+        ref = O.propagate(md, plan.dz, phis[b // 2].astype(np.float32).astype(np.float64), U0[b].astype(np.complex64))
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+
+
+def test_ar_evolution_matches_oracle():
+    # Eq. 4-5 with wind tilt, 4 steps, subharmonics on
+    N, dx, S, alpha = 256, 1e-3, 3, 0.99
+    dz, cn2 = [100.0] * S, [1e-14] * S
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, sh_levels=3, max_batch=1)
+    spec = torch.zeros((S, N, N), dtype=torch.complex64, device=DEV)
+    sh = torch.zeros((S, 27), dtype=torch.complex128, device=DEV)
+    phi = torch.zeros((S, N, N), dtype=torch.float32, device=DEV)
+    seed, real, vx, vy, T = 99, 5, 3.0, -1.5, 1e-3
+    ref_spec, ref_sh = [], []
+    for s in range(S):
+        a, b = O.screen_spectrum(md, cn2[s], dz[s], 3, seed, s, real, 0)
+        ref_spec.append(a)
+        ref_sh.append(b)
+    for t in range(0, 5):
+        plan.evolve_screens(spec, phi, seed, t, alpha, real=real, vx=vx, vy=vy, T=T, sh_state=sh)
+        torch.cuda.synchronize()
+        for s in range(S):
+            if t > 0:
+                ref_spec[s], ref_sh[s] = O.ar_step(md, cn2[s], dz[s], 3, seed, s, real, t, alpha, ref_spec[s],
+                                                   ref_sh[s], vx=vx, vy=vy, T=T)
+            ref_phi = O.screen_from_spectrum(md, ref_spec[s], ref_sh[s])
+            assert rel_l2(spec[s].cpu().numpy(), ref_spec[s]) < TOL
+            assert rel_l2(sh[s].cpu().numpy().reshape(3, 9), ref_sh[s]) < 1e-12
+            assert rel_l2(phi[s].cpu().numpy(), ref_phi) < TOL, (t, s, rel_l2(phi[s].cpu().numpy(), ref_phi))
+
+
+def test_adjoint_matches_oracle_and_is_the_adjoint():
+    N, dx, S, B = 128, 2e-3, 5, 3
+    seed = 17
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [200.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    rng = np.random.default_rng(6)
+    g0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    x0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    g = torch.from_numpy(g0).to(DEV)
+    plan.propagate_backward(g, B, phi=None, seed=seed, real_base=2)  # screens regenerated from the seed
+    x = torch.from_numpy(x0).to(DEV)
+    plan.propagate(x, B, phi=None, seed=seed, real_base=2)
+    torch.cuda.synchronize()
+    G, X = g.cpu().numpy(), x.cpu().numpy()
+    for b in range(B):
+        phis = np.stack([O.make_screen(md, 1e-14, 200.0, 0, seed, s, 2 + b) for s in range(S)])
+        ref = O.propagate_adjoint(md, [200.0] * S, phis, g0[b])
+        assert rel_l2(G[b], ref) < TOL, rel_l2(G[b], ref)
+        # <P x, g> = <x, P^H g>
+        lhs = np.vdot(g0[b].astype(np.complex128), X[b].astype(np.complex128))
+        rhs = np.vdot(G[b].astype(np.complex128), x0[b].astype(np.complex128))
+        assert abs(lhs - rhs) < 1e-5 * np.linalg.norm(g0[b]) * np.linalg.norm(x0[b])
+
+
+def test_autograd_function_uses_the_adjoint():
+    N, dx, S = 128, 2e-3, 3
+    plan = ts.Plan(LAM, N, dx, [200.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy((rng.standard_normal((2, N, N)) + 1j * rng.standard_normal((2, N, N))).astype(np.complex64))
+    x = x.to(DEV).requires_grad_(True)
+    w = torch.rand((N, N), device=DEV)
+    y = ts.propagate(x, plan, seed=5)
+    loss = (w * y.abs() ** 2).sum()
+    loss.backward()
+    g_out = (2 * w * y.detach()).contiguous()
+    ref = g_out.clone()
+    plan.propagate_backward(ref, 2, seed=5)
+    torch.cuda.synchronize()
+    assert torch.allclose(x.grad, ref)
+
+
+def test_moments_and_beam_sums_match_oracle():
+    # plane wave and Gaussian sharing screens per realization (two moment groups), two chunks
+    N, dx, S, R = 128, 2e-3, 3, 6
+    seed = 0x2604072480 + 2
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [300.0] * S, [3e-14] * S, l0=5e-3, L0=10.0, max_batch=2 * R)
+    plan.set_sources([0.0, 0.03])
+    mean = torch.zeros((2, N, N), dtype=torch.float64, device=DEV)
+    m2 = torch.zeros_like(mean)
+    count = 0
+    ref = [O.Welford((N, N)), O.Welford((N, N))]
+    for chunk in range(2):
+        B = R  # R/2 realizations x 2 sources
+        U = cfield(B, N)
+        I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+        sums = torch.zeros((B, 2), dtype=torch.float64, device=DEV)
+        plan.propagate(U, B, phi=None, phi_group=2, flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY, seed=seed,
+                       real_base=chunk * (R // 2), intensity=I, beam_sums=sums)
+        plan.moments_accumulate(I, B, 2, count, mean, m2)
+        count += B // 2
+        torch.cuda.synchronize()
+        Ih = I.cpu().numpy().astype(np.float64)
+        for b in range(B):
+            r = chunk * (R // 2) + b // 2
+            phis = np.stack([O.make_screen(md, 3e-14, 300.0, 0, seed, s, r) for s in range(S)])
+            src = np.ones((N, N), complex) if b % 2 == 0 else O.source_gaussian(N, dx, 0.03)
+            Iref = np.abs(O.propagate(md, [300.0] * S, phis, src)) ** 2
+            assert rel_l2(Ih[b], Iref) < 2 * TOL
+            sI, sR = O.beam_sums(N, dx, Iref)
+            assert abs(sums[b, 0].item() / sI - 1) < 2 * TOL and abs(sums[b, 1].item() / sR - 1) < 2 * TOL
+            ref[b % 2].update(Ih[b])  # same intensities: isolates the moment arithmetic
+    si_map = torch.zeros_like(mean)
+    si_mean = torch.zeros(2, dtype=torch.float64, device=DEV)
+    si_c = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.moments_finalize(mean, m2, 2, count, si_map=si_map, si_mean=si_mean, si_center=si_c)
+    torch.cuda.synchronize()
+    for g in range(2):
+        assert rel_l2(mean[g].cpu().numpy(), ref[g].mean) < 1e-12
+        assert rel_l2(m2[g].cpu().numpy(), ref[g].M2) < 1e-10
+        si = ref[g].si_map()
+        assert rel_l2(si_map[g].cpu().numpy(), si) < 1e-10
+        assert abs(si_mean[g].item() / si.mean() - 1) < 1e-10
+        assert abs(si_c[g].item() / si[N // 2, N // 2] - 1) < 1e-10
+
+
+def test_config3_full_size_sampled_beams():
+    # N = 1024, dx = 0.5 mm, 16 screens of 62.5 m, Cn^2 = 1e-15, AR alpha = 0.99, 8 beams
+    # w0 = 1.0 + 0.25 b cm, in the launch configuration the benchmark times (B = 8, phi_group = 8);
+    # beams 0 and 7 after one AR step are checked against the oracle.
+    N, dx, S, alpha = 1024, 5e-4, 16, 0.99
+    seed = 0x2604072480 + 3
+    dz, cn2 = [62.5] * S, [1e-15] * S
+    plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, max_batch=8)
+    w0 = [0.01 + 0.0025 * b for b in range(8)]
+    plan.set_sources(w0)
+    spec = torch.zeros((S, N, N), dtype=torch.complex64, device=DEV)
+    phi = torch.zeros((S, N, N), dtype=torch.float32, device=DEV)
+    U = cfield(8, N)
+    plan.evolve_screens(spec, phi, seed, 0, alpha)
+    plan.evolve_screens(spec, phi, seed, 1, alpha)
+    plan.propagate(U, 8, phi=phi, phi_group=8, flags=ts.TS_PROP_SOURCE)
+    torch.cuda.synchronize()
+    md = omedium(N, dx)
+    ref_phi = []
+    for s in range(S):
+        sp, _ = O.screen_spectrum(md, cn2[s], dz[s], 0, seed, s, 0, 0)
+        sp, _ = O.ar_step(md, cn2[s], dz[s], 0, seed, s, 0, 1, alpha, sp)
+        ref_phi.append(O.screen_from_spectrum(md, sp))
+        if s in (0, 15):
+            assert rel_l2(phi[s].cpu().numpy(), ref_phi[-1]) < TOL
+    ref_phi = np.stack(ref_phi)
+    for b in (0, 7):
+        ref = O.propagate(md, dz, ref_phi, O.source_gaussian(N, dx, w0[b]))
+        assert rel_l2(U[b].cpu().numpy(), ref) < TOL, (b, rel_l2(U[b].cpu().numpy(), ref))
+
+
+def test_large_grid_2048_and_energy():
+    N, dx, S = 2048, 2e-3, 2
+    plan = ts.Plan(LAM, N, dx, [300.0] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=1)
+    plan.set_sources([0.05])
+    U = cfield(1, N)
+    plan.propagate(U, 1, seed=3, flags=ts.TS_PROP_SOURCE)
+    torch.cuda.synchronize()
+    md = omedium(N, dx)
+    phis = np.stack([O.make_screen(md, 1e-15, 300.0, 0, 3, s, 0) for s in range(S)])
+    ref = O.propagate(md, [300.0] * S, phis, O.source_gaussian(N, dx, 0.05))
+    assert rel_l2(U[0].cpu().numpy(), ref) < TOL
+
+
+def test_errors_are_reported_not_launched():
+    plan = ts.Plan(LAM, 128, 2e-3, [200.0], [1e-15], max_batch=2)
+    U = cfield(3, 128)
+    with pytest.raises(ts.TsError) as ei:
+        plan.propagate(U, 3)
+    assert ei.value.status == 3
+    with pytest.raises(ts.TsError):
+        plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE)  # no source table set
+    with pytest.raises(ts.TsError):
+        plan.propagate(U, 1, flags=ts.TS_PROP_INTENSITY)  # intensity buffer missing
