@@ -177,12 +177,15 @@ ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2
  * (device float32 [N][N]): kind 0 = mean |I - Iref| (MAE, Sec. 2.5), kind 1 = mean (I - Iref)^2,
  * mean over batch and pixels; written to loss (device float64 [1]).
  * th1, th2: device float32 [N][N].  ws: device complex64 workspace [3][B][N][N] kept for the
- * backward call (Z1, W2, V). */
+ * backward call (Z1, W2, V); intensity: device float32 [B][N][N], written (also kept for the
+ * backward call).  B <= max_batch.  N must be divisible by 4 (all supported N are). */
 ts_status ts_d2nn_forward(ts_plan plan, const void* U, int B, const float* th1, const float* th2, double aperture,
                           const float* Iref, int kind, void* ws, float* intensity, double* loss, void* stream);
 
 /* Adjoint of ts_d2nn_forward: writes dL/dth1, dL/dth2 (device float32 [N][N], sums over the
- * batch) and dL/dU (device complex64 [B][N][N]) from the workspace of the forward call:
+ * batch in increasing b) and dL/dU (device complex64 [B][N][N]) from the workspace and intensity of
+ * the forward call (same th1, th2, aperture, Iref, kind).  The workspace is consumed: per-field
+ * mask gradients overwrite Z1 and W2, so a second backward needs a new forward call.
  *   g_V = 2 V dL/dI; g_W2 = C(g_V); dL/dth2 = sum Im(g_W2 conj W2); g_Z1 = C^-1(exp(-i th2) g_W2);
  *   dL/dth1 = sum Im(g_Z1 conj Z1); dL/dU = A exp(-i th1) g_Z1. */
 ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* th2, double aperture,

@@ -23,7 +23,7 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, field, plan, phi, phi_group, seed, real_base):
-            out = field.detach().clone().contiguous()
+            out = field.detach().resolve_conj().contiguous().clone()
             B = out.shape[0] if out.dim() == 3 else 1
             plan.propagate(out, B, phi=phi, phi_group=phi_group, seed=seed, real_base=real_base)
             ctx.plan, ctx.phi, ctx.meta = plan, phi, (B, phi_group, seed, real_base)
@@ -32,7 +32,7 @@ def _autograd():
         @staticmethod
         def backward(ctx, grad):
             B, phi_group, seed, real_base = ctx.meta
-            g = grad.detach().clone().contiguous()
+            g = grad.detach().resolve_conj().contiguous().clone()
             ctx.plan.propagate_backward(g, B, phi=ctx.phi, phi_group=phi_group, seed=seed, real_base=real_base)
             return g, None, None, None, None, None
 

@@ -97,9 +97,14 @@ def _check(status: int, where: str):
 
 
 def _ptr(t) -> int | None:
-    """Device pointer of a tensor (or None)."""
+    """Device pointer of a tensor (or None).  The C ABI reads raw memory, so lazily conjugated or
+    non-contiguous views are rejected rather than passed with the wrong contents."""
     if t is None:
         return None
+    if getattr(t, "is_conj", None) is not None and t.is_conj():
+        raise ValueError("tensor has a pending conjugation (call .resolve_conj())")
+    if getattr(t, "is_contiguous", None) is not None and not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
     return t.data_ptr()
 
 

@@ -236,6 +236,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     ok(build_tables(*p));
     ok(prepare_prop_kernels(N));
     ok(prepare_screen_kernels(N));
+    ok(prepare_d2nn_kernels(N));
     if (e != cudaSuccess) {
         ts_status st = cuda_check(e, "ts_plan_create tables");
         free_plan(p);
@@ -498,16 +499,52 @@ ts_status ts_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, in
     return cuda_check(launch_philox(ctr, key0, key1, n, out, as_stream(stream)), "ts_philox4x32_10");
 }
 
-ts_status ts_d2nn_forward(ts_plan, const void*, int, const float*, const float*, double, const float*, int, void*, float*,
-                          double*, void*)
+ts_status ts_d2nn_forward(ts_plan plan, const void* U, int B, const float* th1, const float* th2, double aperture,
+                          const float* Iref, int kind, void* ws, float* intensity, double* loss, void* stream)
 {
-    return fail(TS_ERR_UNSUPPORTED, "ts_d2nn_forward: not available in this build");
+    if (!plan || !U || !th1 || !th2 || !Iref || !ws || !intensity || !loss)
+        return fail(TS_ERR_INVALID_ARG, "ts_d2nn_forward: null pointer");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (B < 1 || (kind != 0 && kind != 1) || !(aperture > 0.0))
+        return fail(TS_ERR_INVALID_ARG, "ts_d2nn_forward: need B >= 1, kind 0/1 and aperture > 0");
+    if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_d2nn_forward: B exceeds the plan's max_batch");
+    D2nnArgs d{};
+    d.U = reinterpret_cast<const float2*>(U);
+    d.B = B;
+    d.th1 = th1;
+    d.th2 = th2;
+    d.aperture = aperture;
+    d.Iref = Iref;
+    d.kind = kind;
+    d.ws = reinterpret_cast<float2*>(ws);
+    d.I = intensity;
+    d.loss = loss;
+    return cuda_check(launch_d2nn(*p, false, d, as_stream(stream)), "ts_d2nn_forward");
 }
 
-ts_status ts_d2nn_backward(ts_plan, int, const float*, const float*, double, const float*, int, const void*,
-                           const float*, float*, float*, void*, void*)
+ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* th2, double aperture, const float* Iref,
+                           int kind, const void* ws, const float* intensity, float* g_th1, float* g_th2, void* gU,
+                           void* stream)
 {
-    return fail(TS_ERR_UNSUPPORTED, "ts_d2nn_backward: not available in this build");
+    if (!plan || !th1 || !th2 || !Iref || !ws || !intensity || !g_th1 || !g_th2 || !gU)
+        return fail(TS_ERR_INVALID_ARG, "ts_d2nn_backward: null pointer");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (B < 1 || (kind != 0 && kind != 1) || !(aperture > 0.0))
+        return fail(TS_ERR_INVALID_ARG, "ts_d2nn_backward: need B >= 1, kind 0/1 and aperture > 0");
+    if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_d2nn_backward: B exceeds the plan's max_batch");
+    D2nnArgs d{};
+    d.B = B;
+    d.th1 = th1;
+    d.th2 = th2;
+    d.aperture = aperture;
+    d.Iref = Iref;
+    d.kind = kind;
+    d.ws = reinterpret_cast<float2*>(const_cast<void*>(ws));
+    d.I = const_cast<float*>(intensity);
+    d.g_th1 = g_th1;
+    d.g_th2 = g_th2;
+    d.gU = reinterpret_cast<float2*>(gU);
+    return cuda_check(launch_d2nn(*p, true, d, as_stream(stream)), "ts_d2nn_backward");
 }
 
 }  // extern "C"

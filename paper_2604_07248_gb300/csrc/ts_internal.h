@@ -109,6 +109,25 @@ struct ScreenArgs {
 };
 cudaError_t launch_screens(Plan& p, int mode, const ScreenArgs& a, cudaStream_t st);
 
+// D2NN receiver
+struct D2nnArgs {
+    const float2* U;
+    int B;
+    const float* th1;
+    const float* th2;
+    double aperture;
+    const float* Iref;
+    int kind;
+    float2* ws;      // [3][B][N][N]: Z1, W2, V
+    float* I;
+    double* loss;
+    float* g_th1;
+    float* g_th2;
+    float2* gU;
+};
+cudaError_t launch_d2nn(const Plan& p, bool backward, const D2nnArgs& d, cudaStream_t st);
+cudaError_t prepare_d2nn_kernels(int N);
+
 // moments
 cudaError_t launch_moments(const Plan& p, const float* I, int B, int G, int64_t count, double* mean, double* m2,
                            cudaStream_t st);

@@ -1,0 +1,127 @@
+"""GPU parity of the D2NN receiver and the differentiable path (config 5 shape) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2604_07248_gb300 as ts  # noqa: E402
+
+LAM = 1.55e-6
+DEV = torch.device("cuda:0")
+AP = 0.3048
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+def to_dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x).astype(dtype)).to(DEV)
+
+
+@pytest.mark.parametrize("kind", [1, 0])
+def test_receiver_forward_and_adjoint_match_oracle(kind):
+    N, dx, B = 128, 3e-3, 3
+    rng = np.random.default_rng(10 + kind)
+    U = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))) * 0.1
+    U = U.astype(np.complex64)
+    th1 = rng.normal(0, 0.1, (N, N)).astype(np.float32)
+    th2 = rng.normal(0, 0.1, (N, N)).astype(np.float32)
+    A = O.aperture(N, dx, AP)
+    Iref = (np.abs(O.source_gaussian(N, dx, 0.05)) ** 2 * A * 0.02).astype(np.float32)
+    plan = ts.Plan(LAM, N, dx, [10.0], [0.0], max_batch=B)
+    ws = torch.zeros((3, B, N, N), dtype=torch.complex64, device=DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    dU, t1, t2, dI = to_dev(U, np.complex64), to_dev(th1, np.float32), to_dev(th2, np.float32), to_dev(Iref, np.float32)
+    plan.d2nn_forward(dU, B, t1, t2, AP, dI, kind, ws, I, loss)
+    g1 = torch.zeros((N, N), dtype=torch.float32, device=DEV)
+    g2 = torch.zeros_like(g1)
+    gU = torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+    plan.d2nn_backward(B, t1, t2, AP, dI, kind, ws, I, g1, g2, gU)
+    torch.cuda.synchronize()
+    L_ref = 0.0
+    rg1, rg2 = np.zeros((N, N)), np.zeros((N, N))
+    gU_ref = []
+    mism = np.zeros((B, N, N), bool)
+    for b in range(B):
+        Ib, Z1, W2, V = O.d2nn_forward(A, th1.astype(np.float64), th2.astype(np.float64), U[b])
+        assert rel_l2(I[b].cpu().numpy(), Ib) < 1e-5
+        Lb, dLdI = O.intensity_loss(Ib, Iref.astype(np.float64), kind, B * N * N)
+        L_ref += Lb
+        mism[b] = np.sign(I[b].cpu().numpy() - Iref) != np.sign(Ib - Iref)
+        gU_ref.append(O.d2nn_backward(A, th1.astype(np.float64), th2.astype(np.float64), Z1, W2, V, dLdI, rg1, rg2))
+    assert abs(loss.item() / L_ref - 1) < 1e-6
+    if kind == 0:
+        # MAE: dL/dI = sign(I - Iref) may flip where FP32 and FP64 intensities straddle Iref
+        assert mism.mean() < 1e-3
+    tol = 1e-4 if kind == 1 else 2e-2
+    assert rel_l2(g1.cpu().numpy(), rg1) < tol
+    assert rel_l2(g2.cpu().numpy(), rg2) < tol
+    for b in range(B):
+        assert rel_l2(gU[b].cpu().numpy(), gU_ref[b]) < tol
+
+
+def test_differentiable_path_config5_shape():
+    # N = 512, dx = 1 mm, 10 screens of 100 m, Cn^2 = 5e-16, Gaussian w0 = 2 cm, batch 4 of the 64;
+    # masks seeded N(0, 0.1 rad); loss: squared intensity error against the apertured vacuum beam.
+    N, dx, S, B = 512, 1e-3, 10, 4
+    seed = 0x2604072480 + 5
+    dz, cn2 = [100.0] * S, [5e-16] * S
+    plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, max_batch=B)
+    plan.set_sources([0.02])
+    vac = ts.Plan(LAM, N, dx, dz, [0.0] * S, max_batch=1)
+    vac.set_sources([0.02])
+    th1 = np.random.default_rng(seed).normal(0, 0.1, (N, N)).astype(np.float32)
+    th2 = np.random.default_rng(seed + 1).normal(0, 0.1, (N, N)).astype(np.float32)
+    t1, t2 = to_dev(th1, np.float32), to_dev(th2, np.float32)
+    # reference intensity: vacuum field through the zero-phase receiver = |A U_vac|^2
+    Uv = torch.zeros((1, N, N), dtype=torch.complex64, device=DEV)
+    vac.propagate(Uv, 1, flags=ts.TS_PROP_SOURCE)
+    z = torch.zeros((N, N), dtype=torch.float32, device=DEV)
+    ws1 = torch.zeros((3, 1, N, N), dtype=torch.complex64, device=DEV)
+    Iv = torch.zeros((1, N, N), dtype=torch.float32, device=DEV)
+    l1 = torch.zeros(1, dtype=torch.float64, device=DEV)
+    vac.d2nn_forward(Uv, 1, z, z, AP, z, 1, ws1, Iv, l1)
+    Iref = Iv[0].contiguous()
+    # forward through turbulence, receiver, adjoint, adjoint path (screens regenerated from seed)
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+    plan.propagate(U, B, flags=ts.TS_PROP_SOURCE, seed=seed)
+    ws = torch.zeros((3, B, N, N), dtype=torch.complex64, device=DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    Uout = U.clone()
+    plan.d2nn_forward(U, B, t1, t2, AP, Iref, 1, ws, I, loss)
+    g1 = torch.zeros((N, N), dtype=torch.float32, device=DEV)
+    g2 = torch.zeros_like(g1)
+    gU = torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+    plan.d2nn_backward(B, t1, t2, AP, Iref, 1, ws, I, g1, g2, gU)
+    plan.propagate_backward(gU, B, seed=seed)
+    torch.cuda.synchronize()
+
+    md = O.medium(LAM, N, dx, l0=5e-3, L0=10.0)
+    A = O.aperture(N, dx, AP)
+    Uvac = O.propagate(md, dz, None, O.source_gaussian(N, dx, 0.02))
+    Iref_o = np.abs(A * Uvac) ** 2
+    assert rel_l2(Iref.cpu().numpy(), Iref_o) < 1e-5
+    rg1, rg2 = np.zeros((N, N)), np.zeros((N, N))
+    Lo = 0.0
+    for b in range(B):
+        phis = np.stack([O.make_screen(md, cn2[s], dz[s], 0, seed, s, b) for s in range(S)])
+        Ub = O.propagate(md, dz, phis, O.source_gaussian(N, dx, 0.02))
+        assert rel_l2(Uout[b].cpu().numpy(), Ub) < 1e-5
+        Ib, Z1, W2, V = O.d2nn_forward(A, th1.astype(np.float64), th2.astype(np.float64), Ub)
+        Lb, dLdI = O.intensity_loss(Ib, Iref_o, 1, B * N * N)
+        Lo += Lb
+        gUb = O.d2nn_backward(A, th1.astype(np.float64), th2.astype(np.float64), Z1, W2, V, dLdI, rg1, rg2)
+        gin = O.propagate_adjoint(md, dz, phis, gUb)
+        assert rel_l2(gU[b].cpu().numpy(), gin) < 1e-4, rel_l2(gU[b].cpu().numpy(), gin)
+    assert abs(loss.item() / Lo - 1) < 1e-4
+    assert rel_l2(g1.cpu().numpy(), rg1) < 1e-4
+    assert rel_l2(g2.cpu().numpy(), rg2) < 1e-4

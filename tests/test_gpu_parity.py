@@ -56,7 +56,7 @@ def test_philox_words_bit_exact():
 
 @pytest.mark.parametrize("N,dx,sh,n_real,S", [(128, 2e-3, 0, 2, 5), (256, 1e-3, 3, 2, 3), (512, 1e-3, 3, 1, 2)])
 def test_screens_match_oracle(N, dx, sh, n_real, S):
-    dz, cn2 = [200.0] * S, [10 ** -13.5] * S
+    dz, cn2 = [100.0] * S, [10 ** -13.5] * S  # below the Eq. 7 limit (165 m at N = 256, dx = 1 mm)
     plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, sh_levels=sh, max_batch=n_real)
     phi = torch.zeros((n_real, S, N, N), dtype=torch.float32, device=DEV)
     seed = 0x2604072480 + 2
@@ -195,7 +195,14 @@ def test_autograd_function_uses_the_adjoint():
     ref = g_out.clone()
     plan.propagate_backward(ref, 2, seed=5)
     torch.cuda.synchronize()
-    assert torch.allclose(x.grad, ref)
+    # autograd forms dL/dy as 2 w |y| sgn(y) (rounding differs from 2 w y), so compare in L2
+    G, R = x.grad.cpu().numpy(), ref.cpu().numpy()
+    assert np.linalg.norm(G - R) / np.linalg.norm(R) < 1e-6
+    md = omedium(N, dx)
+    for b in range(2):
+        phis = np.stack([O.make_screen(md, 1e-14, 200.0, 0, 5, s, b) for s in range(S)])
+        o = O.propagate_adjoint(md, [200.0] * S, phis, g_out[b].cpu().numpy())
+        assert rel_l2(G[b], o) < TOL
 
 
 def test_moments_and_beam_sums_match_oracle():
