@@ -117,6 +117,22 @@ ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream);
  * uses purpose 1 and word0 = (p - 1) 8 + q / 2. */
 ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* stream);
 
+/* One screen without any device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc where they need a screen (for instance code running under
+ * another framework's allocator or stream rules that forbid new device allocations, or a
+ * latency-critical loop that cannot afford the implicit synchronisation of cudaMalloc/cudaFree).
+ * It computes the same screen as ts_make_screens for a plan whose interval `screen` has length dz
+ * and structure constant cn2 (no subharmonics): phi (device float32 [N][N], written) equals
+ * ts_make_screens' phi[real][screen].  Its twiddles, PSD table and intermediate live in one
+ * fixed-size file-scope device array (about 12 MiB) that every GPU using it holds until the process
+ * exits.  Limits: N <= 1024 (larger N returns TS_ERR_WORKSPACE), screen < 64.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and sets
+ * kernel attributes; make that first call before any CUDA stream capture.  All calls share the
+ * array and each call overwrites it: calls that can overlap on the GPU (different streams without
+ * ordering between them) race and produce wrong screens. */
+ts_status ts_make_screen_noalloc(const ts_medium* medium, const ts_grid* grid, double dz, double cn2, uint64_t seed,
+                                 uint32_t screen, uint32_t real, float* phi, void* stream);
+
 /* AR(1) evolution of the S screens of realization `real` (Sec. 2.3, Eq. 4-5):
  *   t == 0: spec = s(kappa) c^(0)                                   (stationary start)
  *   t >= 1: spec = alpha exp(i theta) spec + sqrt(1 - alpha^2) s(kappa) c^(t),

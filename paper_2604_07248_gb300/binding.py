@@ -64,6 +64,7 @@ SIGNATURES = {
     "ts_philox4x32_10": (_I, [_P, _U32, _U32, _I, _P, _P]),
     "ts_plan_timing": (_I, [_P, _I, _I]),
     "ts_plan_timing_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "ts_make_screen_noalloc": (_I, [C.POINTER(Medium), C.POINTER(Grid), _D, _D, _U64, _U32, _U32, _P, _P]),
     "ts_status_string": (C.c_char_p, [_I]),
     "ts_last_error": (C.c_char_p, []),
 }
@@ -125,6 +126,16 @@ def philox4x32_10(ctr, key0, key1, out, stream=None):
     n = ctr.numel() // 4
     _check(load().ts_philox4x32_10(_ptr(ctr), int(key0), int(key1), n, _ptr(out), _stream(stream)),
            "ts_philox4x32_10")
+
+
+def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0, l0=0.0, L0=0.0, stream=None):
+    """One screen (float32 [N, N] device tensor phi) without any device allocation; see
+    ts_make_screen_noalloc in include/turbscreen.h."""
+    L0v = float(L0) if (L0 is not None and math.isfinite(L0)) else 0.0
+    med = Medium(float(lam), float(n0), float(l0), L0v)
+    _check(load().ts_make_screen_noalloc(C.byref(med), C.byref(Grid(int(N), float(dx))), float(dz), float(cn2),
+                                         int(seed), int(screen), int(real), _ptr(phi), _stream(stream)),
+           "ts_make_screen_noalloc")
 
 
 class Plan:

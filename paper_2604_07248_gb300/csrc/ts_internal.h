@@ -63,6 +63,11 @@ ts_status cuda_check(cudaError_t e, const char* where);
 // tables
 cudaError_t build_tables(Plan& p);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int n, uint32_t* out, cudaStream_t st);
+cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
+cudaError_t launch_psd_shape(int N, float* g, double dk, double L0, double l0, cudaStream_t st);
+// one screen (no subharmonics) from caller-provided tables and intermediate buffer
+cudaError_t launch_screen_raw(int N, const float2* tw, const float* g, const float* amp, float2* y, uint64_t seed,
+                              int screen, uint32_t real, float* phi, cudaStream_t st);
 cudaError_t build_tilt(Plan& p, double vx, double vy, double T, cudaStream_t st);
 
 // propagation passes

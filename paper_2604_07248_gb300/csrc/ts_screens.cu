@@ -357,6 +357,47 @@ cudaError_t launch_screens(Plan& p, int mode, const ScreenArgs& a, cudaStream_t 
     }
 }
 
+cudaError_t launch_screen_raw(int N, const float2* tw, const float* g, const float* amp, float2* y, uint64_t seed,
+                              int screen, uint32_t real, float* phi, cudaStream_t st)
+{
+    ScreenColParams cp{};
+    cp.tw = tw;
+    cp.g = g;
+    cp.amp = amp;
+    cp.y = y;
+    cp.spec = nullptr;
+    cp.tilt = nullptr;
+    cp.k0 = (uint32_t)seed;
+    cp.k1 = (uint32_t)(seed >> 32);
+    cp.s_begin = screen;
+    cp.s_count = 1;
+    cp.r_begin = real;
+    cp.tag = 0;
+    ScreenRowParams rp{};
+    rp.tw = tw;
+    rp.y = y;
+    rp.phi = phi;
+    cudaError_t e = cudaSuccess;
+#define TS_RAW(NN)                                                                                    \
+    case NN: {                                                                                        \
+        e = scol_launch<NN, SC_INDEP>(cp, 1, st);                                                     \
+        if (e != cudaSuccess) return e;                                                               \
+        dim3 grid(NN / SRowCfg<NN>::LPC, 1);                                                          \
+        screen_row_kernel<NN, false><<<grid, SRowCfg<NN>::THREADS, SRowCfg<NN>::smem, st>>>(rp);      \
+        return cudaGetLastError();                                                                    \
+    }
+    switch (N) {
+        TS_RAW(128)
+        TS_RAW(256)
+        TS_RAW(512)
+        TS_RAW(1024)
+        TS_RAW(2048)
+    default: return cudaErrorInvalidValue;
+    }
+#undef TS_RAW
+    return e;
+}
+
 cudaError_t prepare_screen_kernels(int N)
 {
     switch (N) {

@@ -150,6 +150,27 @@ cudaError_t build_tables(Plan& p)
     return cudaDeviceSynchronize();
 }
 
+cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st)
+{
+    switch (N) {
+    case 128: twiddle_kernel<128><<<8, 256, 0, st>>>(tw); break;
+    case 256: twiddle_kernel<256><<<8, 256, 0, st>>>(tw); break;
+    case 512: twiddle_kernel<512><<<8, 256, 0, st>>>(tw); break;
+    case 1024: twiddle_kernel<1024><<<8, 256, 0, st>>>(tw); break;
+    case 2048: twiddle_kernel<2048><<<8, 256, 0, st>>>(tw); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psd_shape(int N, float* g, double dk, double L0, double l0, cudaStream_t st)
+{
+    const double k0sq = (L0 > 0.0 && isfinite(L0)) ? (2.0 * M_PI / L0) * (2.0 * M_PI / L0) : 0.0;
+    const double inv_kmsq = l0 > 0.0 ? 1.0 / ((2.0 * M_PI / l0) * (2.0 * M_PI / l0)) : 0.0;
+    psd_shape_kernel<<<1024, 256, 0, st>>>(g, N, dk, k0sq, inv_kmsq);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int n, uint32_t* out, cudaStream_t st)
 {
     philox_kernel<<<(n + 255) / 256, 256, 0, st>>>(ctr, k0, k1, n, out);
