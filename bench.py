@@ -119,13 +119,13 @@ def algorithmic_bytes(N, B, S):
     """Bytes one launch of each kernel kind must move (the roofline numerator), per the 2-pass model:
     column pass: field read + write; row passes: field read + write, screen read once (shared by the
     beams), the first pass writes only; screen synthesis: AR state read + write, column-transformed
-    spectrum write + read, screen write, PSD shape read once."""
+    spectrum write + read, screen phasor write (8 B), PSD shape read once."""
     px = N * N
     col = 16 * B * px
     row_first = 8 * B * px
-    row_mid = 16 * B * px + 4 * px
+    row_mid = 16 * B * px + 8 * px
     row_avg = (row_first + S * row_mid) / (S + 1)
-    screens = S * 36 * px + 4 * px
+    screens = S * 40 * px + 4 * px
     return {0: col, 1: row_avg, 2: screens}
 
 
@@ -163,7 +163,9 @@ def run_gpu(args):
     plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
     plan.set_sources(wl.w0)
     spec = torch.zeros((S, N, N), dtype=torch.complex64, device=dev)
-    phi = torch.zeros((S, N, N), dtype=torch.float32, device=dev)
+    # the screens go straight to their phasors exp(i phi): each screen's sincos is taken once, not
+    # once per beam
+    phasor = torch.zeros((S, N, N), dtype=torch.complex64, device=dev)
     U = torch.zeros((B, N, N), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
     real = rank  # each rank evolves its own independent realization
@@ -171,9 +173,9 @@ def run_gpu(args):
 
     def step(src_from_field=False):
         t = t_next[0]
-        plan.evolve_screens(spec, phi, wl.seed, t, wl.alpha, real=real, stream=stream)
+        plan.evolve_screens(spec, None, wl.seed, t, wl.alpha, real=real, phasor=phasor, stream=stream)
         flags = 0 if src_from_field else ts.TS_PROP_SOURCE
-        plan.propagate(U, B, phi=phi, phi_group=B, flags=flags, stream=stream)
+        plan.propagate(U, B, phasor=phasor, phi_group=B, flags=flags, stream=stream)
         t_next[0] = t + 1
 
     def barrier():
@@ -239,27 +241,50 @@ def run_gpu(args):
             "kernels": per_kernel}
 
     # end to end through the public API with host buffers: per step, H2D of the 8 input fields from
-    # pinned memory, the screen update and propagation, D2H of the 8 receiver fields
+    # pinned memory, the screen update and propagation, D2H of the 8 receiver fields.  Two device
+    # field buffers and two copy streams let step t's copies overlap steps t-1 / t+1's compute.
     e2e = None
     if not args.no_e2e:
-        host_in = torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True)
-        host_out = torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True)
-        plan.make_sources(U, B, stream=stream)  # the 8 source fields become the host-side input
-        host_in.copy_(U)
         n_e2e = min(args.steps, 256)
+        host_in = torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True)
+        host_out = [torch.empty((B, N, N), dtype=torch.complex64, pin_memory=True) for _ in range(2)]
+        dbuf = [torch.empty((B, N, N), dtype=torch.complex64, device=dev) for _ in range(2)]
+        plan.make_sources(dbuf[0], B, stream=stream)  # the 8 source fields are the host-side input
+        host_in.copy_(dbuf[0])
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        for k in range(2):
+            ev_out[k].record(s_out)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(n_e2e):
-            U.copy_(host_in, non_blocking=True)
-            step(src_from_field=True)
-            host_out.copy_(U, non_blocking=True)
+        s_in.wait_event(f0)
+        for i in range(n_e2e):
+            k = i % 2
+            s_in.wait_event(ev_out[k])          # the buffer's previous result has left the device
+            with torch.cuda.stream(s_in):
+                dbuf[k].copy_(host_in, non_blocking=True)
+            ev_in[k].record(s_in)
+            stream.wait_event(ev_in[k])
+            tt = t_next[0]
+            plan.evolve_screens(spec, None, wl.seed, tt, wl.alpha, real=real, phasor=phasor, stream=stream)
+            plan.propagate(dbuf[k], B, phasor=phasor, phi_group=B, stream=stream)
+            t_next[0] = tt + 1
+            ev_done[k].record(stream)
+            s_out.wait_event(ev_done[k])
+            with torch.cuda.stream(s_out):
+                host_out[k].copy_(dbuf[k], non_blocking=True)
+            ev_out[k].record(s_out)
+        stream.wait_stream(s_out)
         f1.record(stream)
         barrier()
         ms_e2e = max_over_ranks(f0.elapsed_time(f1))
         e2e = {"value": round(n_e2e * B * S * world / (ms_e2e * 1e-3), 1), "unit": UNIT,
                "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
-               "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()), "steps": n_e2e}
+               "d2h_bytes_per_step": int(host_out[0].numel() * host_out[0].element_size()), "steps": n_e2e,
+               "pipeline": "double-buffered fields, H2D and D2H on their own streams overlapping compute"}
 
     value = args.steps * B * S * world / (ms * 1e-3)
     res = {
@@ -269,7 +294,9 @@ def run_gpu(args):
         "config": {"workload": wl.name, "N": N, "dx": wl.dx, "L": wl.L, "screens": S, "beams": B,
                    "cn2": wl.cn2[0], "alpha": wl.alpha, "field_screen_steps_per_step": B * S,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "working set 256 MiB (AR spectra 128 + screens 64 + fields 64) > 126 MB L2; no flush"},
+                   "autotune": dict(zip(("points_per_thread", "us_e16", "us_e32"),
+                                        [round(x, 2) if isinstance(x, float) else x for x in plan.tuning()])),
+                   "l2": "working set 320 MiB (AR spectra 128 + screen phasors 128 + fields 64) > 126 MB L2; no flush"},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

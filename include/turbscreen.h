@@ -94,6 +94,12 @@ ts_status ts_plan_destroy(ts_plan plan);
 /* Device bytes held by the plan (tables + workspace). */
 size_t ts_plan_device_bytes(ts_plan plan);
 
+/* Autotuner result of the plan: the propagation passes run with `points_per_thread` FFT points
+ * per thread (16 or 32); us_e16 / us_e32 (either may be NULL) receive the timed cost in microseconds
+ * of one column + one row pass for each candidate (0 when not timed: N <= 256, a cached result, or
+ * TS_FFT_E set in the environment). */
+ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32);
+
 /* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
  * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */
 double ts_max_step(const ts_medium* medium, const ts_grid* grid);
@@ -111,11 +117,13 @@ ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream);
  * [real_base, real_base + n_real) and screen s in [0, S):
  *   phi = Re(sum_kappa s(kappa) c(kappa) exp(+i kappa.x)) + phi_SH - mean,
  * s(kappa) = sqrt(Phi_phi(kappa)) dkappa with s(0) = 0, c = Philox4x32-10 complex Gaussian noise.
- * phi: device float32 [n_real][S][N][N], written.  Counter layout of the noise:
+ * phi: device float32 [n_real][S][N][N] and/or phasor: device complex64 [n_real][S][N][N] holding
+ * exp(i phi) (either may be NULL, not both), written.  Counter layout of the noise:
  * key = (seed mod 2^32, seed >> 32), counter = (word0, s, r, (purpose << 24) | t) with t = 0;
  * grid bins (m, n) and (m + N/2, n) share word0 = m N + n (m < N/2); subharmonic cell q of level p
  * uses purpose 1 and word0 = (p - 1) 8 + q / 2. */
-ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* stream);
+ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* phasor,
+                          void* stream);
 
 /* One screen without any device allocation.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc where they need a screen (for instance code running under
@@ -141,9 +149,10 @@ ts_status ts_make_screen_noalloc(const ts_medium* medium, const ts_grid* grid, d
  * by the same rule with their own frequencies.
  * spec: device complex64 [S][N][N], read (t >= 1) and written.  sh_state: device complex128
  * [S][27] when the plan has subharmonics (else NULL), read/written likewise.  phi: device float32
- * [S][N][N], written.  0 <= alpha <= 1. */
+ * [S][N][N] and/or phasor: device complex64 [S][N][N] = exp(i phi), written (either may be NULL,
+ * not both).  0 <= alpha <= 1. */
 ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t t, double alpha, double vx,
-                            double vy, double T, void* spec, void* sh_state, float* phi, void* stream);
+                            double vy, double T, void* spec, void* sh_state, float* phi, void* phasor, void* stream);
 
 /* ts_propagate flags */
 #define TS_PROP_SOURCE 1    /* start from the plan's source table instead of reading `field`     */
@@ -155,21 +164,23 @@ ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t
  *   piston exp(i k dz_s)), FFT2 unnormalised, IFFT2 with 1/N^2.
  * field: device complex64 [B][N][N], input (unless TS_PROP_SOURCE) and output.
  * phi: device float32 screens [G][S][N][N] with G = ceil(B / phi_group): field b uses screen set
- * b / phi_group.  phi == NULL regenerates the screens from (seed, real_base + b / phi_group)
- * exactly as ts_make_screens does (plan workspace; no allocation).
+ * b / phi_group.  phasor: the same screens as exp(i phi), device complex64 [G][S][N][N]; when given
+ * it is used instead of phi (one complex multiply per point instead of a sincos, which pays off when
+ * several fields share a screen).  Both NULL regenerates the screens from
+ * (seed, real_base + b / phi_group) exactly as ts_make_screens does (plan workspace; no allocation).
  * intensity: device float32 [B][N][N] (TS_PROP_INTENSITY) else NULL.
  * beam_sums: device float64 [B][2] or NULL: per field sum I and sum r^2 I (r from pixel (N/2, N/2)).
  * Errors: TS_ERR_INVALID_ARG, TS_ERR_WORKSPACE (B > max_batch), TS_ERR_CUDA. */
-ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int phi_group, int flags, uint64_t seed,
-                       uint32_t real_base, float* intensity, double* beam_sums, void* stream);
+ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, const void* phasor, int phi_group, int flags,
+                       uint64_t seed, uint32_t real_base, float* intensity, double* beam_sums, void* stream);
 
 /* Adjoint of ts_propagate with respect to the input field: grad <- P^H grad, i.e. for s = S-1..0
  *   g <- g exp(-i phi_s);  g <- IFFT2(FFT2(g) conj(H_s)).
- * grad: device complex64 [B][N][N] in/out (dL/dU_out in, dL/dU_in out).  phi as in ts_propagate;
- * NULL regenerates each screen from its seed (bit-identical to the forward screens) one step at a
- * time in the plan workspace instead of storing them. */
-ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, int phi_group, uint64_t seed,
-                                uint32_t real_base, void* stream);
+ * grad: device complex64 [B][N][N] in/out (dL/dU_out in, dL/dU_in out).  phi / phasor as in
+ * ts_propagate; both NULL regenerates each screen from its seed (bit-identical to the forward
+ * screens) one step at a time in the plan workspace instead of storing them. */
+ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, const void* phasor, int phi_group,
+                                uint64_t seed, uint32_t real_base, void* stream);
 
 /* Per-pixel intensity moments across realizations (S25 with Welford's algorithm, Sec. 3.3).
  * intensity: device float32 [B][N][N]; fields b with b mod n_groups == g form the chunk of group g

@@ -50,13 +50,14 @@ SIGNATURES = {
     "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
     "ts_plan_destroy": (_I, [_P]),
     "ts_plan_device_bytes": (C.c_size_t, [_P]),
+    "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_plan_set_sources": (_I, [_P, _I, _P]),
     "ts_make_sources": (_I, [_P, _P, _I, _P]),
-    "ts_make_screens": (_I, [_P, _U64, _U32, _I, _P, _P]),
-    "ts_evolve_screens": (_I, [_P, _U64, _U32, _U32, _D, _D, _D, _D, _P, _P, _P, _P]),
-    "ts_propagate": (_I, [_P, _P, _I, _P, _I, _I, _U64, _U32, _P, _P, _P]),
-    "ts_propagate_backward": (_I, [_P, _P, _I, _P, _I, _U64, _U32, _P]),
+    "ts_make_screens": (_I, [_P, _U64, _U32, _I, _P, _P, _P]),
+    "ts_evolve_screens": (_I, [_P, _U64, _U32, _U32, _D, _D, _D, _D, _P, _P, _P, _P, _P]),
+    "ts_propagate": (_I, [_P, _P, _I, _P, _P, _I, _I, _U64, _U32, _P, _P, _P]),
+    "ts_propagate_backward": (_I, [_P, _P, _I, _P, _P, _I, _U64, _U32, _P]),
     "ts_moments_accumulate": (_I, [_P, _P, _I, _I, _I64, _P, _P, _P]),
     "ts_moments_finalize": (_I, [_P, _P, _P, _I, _I64, _P, _P, _P, _P]),
     "ts_d2nn_forward": (_I, [_P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
@@ -168,6 +169,12 @@ class Plan:
     def device_bytes(self) -> int:
         return load().ts_plan_device_bytes(self._h)
 
+    def tuning(self):
+        """(points per thread chosen for the propagation passes, us for E=16, us for E=32)."""
+        e, a, b = C.c_int(), C.c_float(), C.c_float()
+        _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b)), "ts_plan_tuning")
+        return e.value, a.value, b.value
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().ts_plan_destroy(self._h)
@@ -196,24 +203,25 @@ class Plan:
     def make_sources(self, field, B, stream=None):
         _check(load().ts_make_sources(self._h, _ptr(field), int(B), _stream(stream)), "ts_make_sources")
 
-    def make_screens(self, phi, seed, real_base=0, n_real=1, stream=None):
-        _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _stream(stream)),
-               "ts_make_screens")
+    def make_screens(self, phi, seed, real_base=0, n_real=1, phasor=None, stream=None):
+        _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _ptr(phasor),
+                                      _stream(stream)), "ts_make_screens")
 
-    def evolve_screens(self, spec, phi, seed, t, alpha, real=0, vx=0.0, vy=0.0, T=0.0, sh_state=None, stream=None):
+    def evolve_screens(self, spec, phi, seed, t, alpha, real=0, vx=0.0, vy=0.0, T=0.0, sh_state=None, phasor=None,
+                       stream=None):
         _check(load().ts_evolve_screens(self._h, int(seed), int(real), int(t), float(alpha), float(vx), float(vy),
-                                        float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _stream(stream)),
-               "ts_evolve_screens")
+                                        float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _ptr(phasor),
+                                        _stream(stream)), "ts_evolve_screens")
 
     def propagate(self, field, B, phi=None, phi_group=1, flags=0, seed=0, real_base=0, intensity=None,
-                  beam_sums=None, stream=None):
-        _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), int(phi_group), int(flags), int(seed),
-                                   int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream)),
+                  beam_sums=None, phasor=None, stream=None):
+        _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), _ptr(phasor), int(phi_group), int(flags),
+                                   int(seed), int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream)),
                "ts_propagate")
 
-    def propagate_backward(self, grad, B, phi=None, phi_group=1, seed=0, real_base=0, stream=None):
-        _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), int(phi_group), int(seed),
-                                            int(real_base), _stream(stream)), "ts_propagate_backward")
+    def propagate_backward(self, grad, B, phi=None, phi_group=1, seed=0, real_base=0, phasor=None, stream=None):
+        _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), _ptr(phasor), int(phi_group),
+                                            int(seed), int(real_base), _stream(stream)), "ts_propagate_backward")
 
     def moments_accumulate(self, intensity, B, n_groups, count, mean, m2, stream=None):
         _check(load().ts_moments_accumulate(self._h, _ptr(intensity), int(B), int(n_groups), int(count), _ptr(mean),

@@ -4,8 +4,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "ts_internal.h"
 
@@ -81,7 +85,8 @@ void free_plan(Plan* p)
 {
     destroy_events(p);
     void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
-                    p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows};
+                    p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows,
+                    p->tw16 != p->tw ? p->tw16 : nullptr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -99,8 +104,85 @@ ts_status regen_screen(Plan& p, uint64_t seed, uint32_t real_base, int G, int s,
     a.r_begin = real_base;
     a.items = G;
     a.t = 0;
-    a.phi = p.ws_phi;
+    a.phi = nullptr;
+    a.phasor = p.ws_phi;
     return cuda_check(timed(p, 2, st, [&] { return launch_screens(p, SC_INDEP, a, st); }), "screen synthesis");
+}
+
+// Autotuner: for N >= 512 the propagation passes exist with E = 16 and E = 32 points per thread
+// (different register / occupancy / exchange trade-offs).  Each candidate runs one column pass and
+// one middle row pass on B_t workspace fields (2 warm-up + 5 timed repetitions, CUDA events) and the
+// faster one is kept.  Results are cached per (device, N, B_t, transfer form); TS_FFT_E=16|32 forces
+// a choice.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+
+ts_status autotune(Plan& p)
+{
+    if (p.N <= 256) {
+        p.fft_e = 16;
+        return TS_OK;
+    }
+    if (const char* env = std::getenv("TS_FFT_E")) {
+        const int e = std::atoi(env);
+        if (e == 16 || e == 32) {
+            p.fft_e = e;
+            return TS_OK;
+        }
+    }
+    const size_t N2 = (size_t)p.N * p.N;
+    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
+    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p.fft_e = it->second;
+            return TS_OK;
+        }
+    }
+    cudaError_t e = cudaMemset(p.ws_y, 0, sizeof(float2) * N2 * Bt);
+    if (e == cudaSuccess) e = cudaMemset(p.ws_phi, 0, sizeof(float2) * N2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_e = 32;
+    const int cand[2] = {16, 32};
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+        p.fft_e = cand[c];
+        RowArgs ra{};
+        ra.field = p.ws_y;
+        ra.phasor = p.ws_phi;
+        ra.phi_set_stride = 0;
+        ra.phi_group = Bt;
+        ra.phase_sign = 1.0f;
+        ra.B = Bt;
+        auto once = [&]() {
+            cudaError_t x = launch_col_pass(p, 0, false, p.ws_y, Bt, nullptr);
+            if (x == cudaSuccess) x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, nullptr);
+            return x;
+        };
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = once();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = once();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        p.tune_us[c] = ms * 1000.0f / 5.0f;
+        if (e == cudaSuccess && p.tune_us[c] < best) {
+            best = p.tune_us[c];
+            best_e = cand[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune");
+    p.fft_e = best_e;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best_e;
+    return TS_OK;
 }
 
 }  // namespace
@@ -180,6 +262,18 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         tmp.dz[s] = dz;
         tmp.cn2[s] = cn2;
     }
+    // separable transfer function when the dropped terms are negligible for every step:
+    // dz kappa^6 / 16k^5 <= 1e-7 rad and the cross term dz kx^2 ky^2 / 4k^3 <= 0.05 rad
+    {
+        bool sep = true;
+        const double kx2 = std::pow(M_PI / grid->dx, 2.0), k = tmp.k;
+        for (int s = 0; s < tmp.S; ++s) {
+            const double r6 = tmp.dz[s] * kap2max * kap2max * kap2max / (16.0 * std::pow(k, 5.0));
+            const double ex = tmp.dz[s] * kx2 * kx2 / (4.0 * k * k * k);
+            if (r6 > 1e-7 || ex > 0.05) sep = false;
+        }
+        tmp.sep_transfer = sep;
+    }
 
     Plan* p = new Plan(tmp);
     cudaError_t e = cudaGetDevice(&p->device);
@@ -194,6 +288,8 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         if (e == cudaSuccess) e = x;
     };
     ok(dalloc(*p, &p->tw, N));
+    if (N >= 512) ok(dalloc(*p, &p->tw16, N));
+    else p->tw16 = p->tw;
     ok(dalloc(*p, &p->P, (size_t)S * N));
     ok(dalloc(*p, &p->amp, S));
     ok(dalloc(*p, &p->g, N2));
@@ -208,7 +304,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         ok(dalloc(*p, &p->ws_sha, (size_t)p->screen_chunk * kShCoef));
     }
     ok(dalloc(*p, &p->ws_y, (size_t)p->screen_chunk * N2));
-    ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * N2));
+    ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * N2));  // regenerated screens as exp(i phi)
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
     if (e != cudaSuccess) {
         ts_status st = cuda_check(e, "ts_plan_create allocation");
@@ -242,6 +338,13 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         free_plan(p);
         return st;
     }
+    {
+        ts_status st = autotune(*p);
+        if (st != TS_OK) {
+            free_plan(p);
+            return st;
+        }
+    }
     *out = reinterpret_cast<ts_plan>(p);
     return TS_OK;
 }
@@ -256,6 +359,16 @@ ts_status ts_plan_destroy(ts_plan plan)
 }
 
 size_t ts_plan_device_bytes(ts_plan plan) { return plan ? reinterpret_cast<Plan*>(plan)->bytes : 0; }
+
+ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32)
+{
+    if (!plan || !points_per_thread) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning: need plan and output");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    *points_per_thread = p->fft_e;
+    if (us_e16) *us_e16 = p->tune_us[0];
+    if (us_e32) *us_e32 = p->tune_us[1];
+    return TS_OK;
+}
 
 ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0)
 {
@@ -278,9 +391,11 @@ ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream)
     return cuda_check(launch_row_pass(*p, RP_IN_SOURCE | RP_STORE, ra, as_stream(stream)), "ts_make_sources");
 }
 
-ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* stream)
+ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n_real, float* phi, void* phasor,
+                          void* stream)
 {
-    if (!plan || !phi || n_real < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_screens: need plan, phi and n_real >= 1");
+    if (!plan || (!phi && !phasor) || n_real < 1)
+        return fail(TS_ERR_INVALID_ARG, "ts_make_screens: need plan, phi or phasor, and n_real >= 1");
     Plan* p = reinterpret_cast<Plan*>(plan);
     ScreenArgs a{};
     a.seed = seed;
@@ -290,14 +405,16 @@ ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n
     a.items = n_real * p->S;
     a.t = 0;
     a.phi = phi;
+    a.phasor = reinterpret_cast<float2*>(phasor);
     cudaStream_t st = as_stream(stream);
     return cuda_check(timed(*p, 2, st, [&] { return launch_screens(*p, SC_INDEP, a, st); }), "ts_make_screens");
 }
 
 ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t t, double alpha, double vx, double vy,
-                            double T, void* spec, void* sh_state, float* phi, void* stream)
+                            double T, void* spec, void* sh_state, float* phi, void* phasor, void* stream)
 {
-    if (!plan || !spec || !phi) return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: need plan, spec and phi");
+    if (!plan || !spec || (!phi && !phasor))
+        return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: need plan, spec, and phi or phasor");
     Plan* p = reinterpret_cast<Plan*>(plan);
     if (p->sh_levels && !sh_state) return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: plan has subharmonics, sh_state needed");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(TS_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
@@ -317,6 +434,7 @@ ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t
     a.spec = reinterpret_cast<float2*>(spec);
     a.sh_state = reinterpret_cast<double2*>(sh_state);
     a.phi = phi;
+    a.phasor = reinterpret_cast<float2*>(phasor);
     a.tilt = (t > 0) && T != 0.0 && (vx != 0.0 || vy != 0.0);
     a.vx = vx;
     a.vy = vy;
@@ -329,8 +447,8 @@ ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t
                       "ts_evolve_screens");
 }
 
-ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int phi_group, int flags, uint64_t seed,
-                       uint32_t real_base, float* intensity, double* beam_sums, void* stream)
+ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, const void* phasor, int phi_group, int flags,
+                       uint64_t seed, uint32_t real_base, float* intensity, double* beam_sums, void* stream)
 {
     if (!plan || !field) return fail(TS_ERR_INVALID_ARG, "ts_propagate: need plan and field");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -362,15 +480,22 @@ ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int p
         stt = cuda_check(timed(*p, 0, st, [&] { return launch_col_pass(*p, s, false, U, B, st); }),
                          "ts_propagate column pass");
         if (stt != TS_OK) return stt;
-        if (phi) {
+        int rf = RP_IN_FREQ | RP_STORE;
+        ra.phi = nullptr;
+        ra.phasor = nullptr;
+        ra.phi_set_stride = (long long)S * N2;
+        if (phasor) {
+            ra.phasor = reinterpret_cast<const float2*>(phasor) + (size_t)s * N2;
+            rf |= RP_PHASOR;
+        } else if (phi) {
             ra.phi = phi + (size_t)s * N2;
-            ra.phi_set_stride = (long long)S * N2;
+            rf |= RP_PHASE;
         } else {
             if ((stt = regen_screen(*p, seed, real_base, G, s, st)) != TS_OK) return stt;
-            ra.phi = p->ws_phi;
+            ra.phasor = p->ws_phi;
             ra.phi_set_stride = (long long)N2;
+            rf |= RP_PHASOR;
         }
-        int rf = RP_IN_FREQ | RP_PHASE | RP_STORE;
         if (s < S - 1) {
             rf |= RP_OUT_FREQ;
         } else if (flags & TS_PROP_INTENSITY) {
@@ -386,8 +511,8 @@ ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, int p
     return TS_OK;
 }
 
-ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, int phi_group, uint64_t seed,
-                                uint32_t real_base, void* stream)
+ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* phi, const void* phasor, int phi_group,
+                                uint64_t seed, uint32_t real_base, void* stream)
 {
     if (!plan || !grad) return fail(TS_ERR_INVALID_ARG, "ts_propagate_backward: need plan and grad");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -404,28 +529,39 @@ ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* ph
     ra.phase_sign = -1.0f;
     ra.B = B;
     ts_status stt = TS_OK;
+    int phase_flag = RP_PHASOR;
     auto set_screen = [&](int s) -> ts_status {
-        if (phi) {
-            ra.phi = phi + (size_t)s * N2;
-            ra.phi_set_stride = (long long)S * N2;
+        ra.phi = nullptr;
+        ra.phasor = nullptr;
+        ra.phi_set_stride = (long long)S * N2;
+        if (phasor) {
+            ra.phasor = reinterpret_cast<const float2*>(phasor) + (size_t)s * N2;
+            phase_flag = RP_PHASOR;
             return TS_OK;
         }
-        ra.phi = p->ws_phi;
+        if (phi) {
+            ra.phi = phi + (size_t)s * N2;
+            phase_flag = RP_PHASE;
+            return TS_OK;
+        }
+        ra.phasor = p->ws_phi;
         ra.phi_set_stride = (long long)N2;
+        phase_flag = RP_PHASOR;
         return regen_screen(*p, seed, real_base, G, s, st);
     };
     if ((stt = set_screen(S - 1)) != TS_OK) return stt;
-    stt = cuda_check(launch_row_pass(*p, RP_PHASE | RP_OUT_FREQ | RP_STORE, ra, st), "backward first row pass");
+    stt = cuda_check(launch_row_pass(*p, phase_flag | RP_OUT_FREQ | RP_STORE, ra, st), "backward first row pass");
     if (stt != TS_OK) return stt;
     for (int s = S - 1; s >= 0; --s) {
         stt = cuda_check(launch_col_pass(*p, s, true, g, B, st), "backward column pass");
         if (stt != TS_OK) return stt;
         if (s > 0) {
             if ((stt = set_screen(s - 1)) != TS_OK) return stt;
-            stt = cuda_check(launch_row_pass(*p, RP_IN_FREQ | RP_PHASE | RP_OUT_FREQ | RP_STORE, ra, st),
+            stt = cuda_check(launch_row_pass(*p, RP_IN_FREQ | phase_flag | RP_OUT_FREQ | RP_STORE, ra, st),
                              "backward row pass");
         } else {
             ra.phi = nullptr;
+            ra.phasor = nullptr;
             stt = cuda_check(launch_row_pass(*p, RP_IN_FREQ | RP_STORE, ra, st), "backward last row pass");
         }
         if (stt != TS_OK) return stt;

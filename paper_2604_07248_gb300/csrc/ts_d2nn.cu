@@ -43,7 +43,7 @@ struct DRowCfg {
     static constexpr int THREADS = 256;
     static constexpr int LPC = THREADS / C::T;
     static constexpr int LS = C::padded;
-    static constexpr size_t smem = sizeof(float2) * LPC * LS;
+    static constexpr size_t smem = sizeof(float2) * (C::tw_smem + LPC * LS);
 };
 
 template <int N>
@@ -52,7 +52,7 @@ struct DColCfg {
     static constexpr int THREADS = 256;
     static constexpr int W = THREADS / C::T;
     static constexpr int LS = C::padded + (16 / W > 1 ? 16 / W : 1);
-    static constexpr size_t smem = sizeof(float2) * W * LS;
+    static constexpr size_t smem = sizeof(float2) * (C::tw_smem + W * LS);
 };
 
 __device__ __forceinline__ float checker(int i, int j) { return ((i + j) & 1) ? -1.0f : 1.0f; }
@@ -76,7 +76,10 @@ __global__ void __launch_bounds__(256) d2_row_a(const D2Params a)
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int j = blockIdx.x * RC::LPC + line;
     const size_t rowoff = ((size_t)blockIdx.y * N + j) * N;
-    float2* buf = smem + line * RC::LS;
+    float2* tw = smem;
+    float2* buf = smem + C::tw_smem + line * RC::LS;
+    stage_twiddles<N>(tw, a.tw);
+    __syncthreads();
     using Bar = typename std::conditional<(T > 32), BlockBar, WarpBar>::type;
     const float y = (float)(j - N / 2);
     float2 v[E];
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(256) d2_row_a(const D2Params a)
             v[i] = cscale(V, g * checker(x, j));
         }
     }
-    line_fft<N, -1>(v, buf, t, a.tw, Bar());
+    line_fft<N, -1>(v, buf, t, tw, Bar());
 #pragma unroll
     for (int i = 0; i < E; ++i) a.work[rowoff + t + i * T] = v[i];
 }
@@ -114,12 +117,15 @@ __global__ void __launch_bounds__(256) d2_col(const D2Params a)
     extern __shared__ float2 smem[];
     const int c = threadIdx.x % W, t = threadIdx.x / W;
     const int col = blockIdx.x * W + c;
-    float2* buf = smem + c * CC::LS;
+    float2* tw = smem;
+    float2* buf = smem + C::tw_smem + c * CC::LS;
+    stage_twiddles<N>(tw, a.tw);
+    __syncthreads();
     const size_t base = (size_t)blockIdx.y * N * N + col;
     float2 v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = a.work[base + (size_t)(t + i * T) * N];
-    line_fft<N, -1>(v, buf, t, a.tw, BlockBar());
+    line_fft<N, -1>(v, buf, t, tw, BlockBar());
     const float invN = 1.0f / (float)N;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(256) d2_col(const D2Params a)
             v[i] = cmul(v[i], make_float2(cs * invN * invN, -sn * invN * invN));
         }
     }
-    line_fft<N, +1>(v, buf, t, a.tw, BlockBar());
+    line_fft<N, +1>(v, buf, t, tw, BlockBar());
 #pragma unroll
     for (int i = 0; i < E; ++i) a.work[base + (size_t)(t + i * T) * N] = v[i];
 }
@@ -155,12 +161,15 @@ __global__ void __launch_bounds__(256) d2_row_b(const D2Params a)
     const int j = blockIdx.x * RC::LPC + line;
     const int b = blockIdx.y;
     const size_t rowoff = ((size_t)b * N + j) * N;
-    float2* buf = smem + line * RC::LS;
+    float2* tw = smem;
+    float2* buf = smem + C::tw_smem + line * RC::LS;
+    stage_twiddles<N>(tw, a.tw);
+    __syncthreads();
     using Bar = typename std::conditional<(T > 32), BlockBar, WarpBar>::type;
     float2 v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = a.work[rowoff + t + i * T];
-    line_fft<N, +1>(v, buf, t, a.tw, Bar());
+    line_fft<N, +1>(v, buf, t, tw, Bar());
     const float y = (float)(j - N / 2);
     if constexpr (!BACKWARD) {
         double acc = 0.0;

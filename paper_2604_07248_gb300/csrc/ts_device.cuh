@@ -179,12 +179,13 @@ __device__ __forceinline__ void dft_strided(float2* v)
 }
 
 // ----------------------------------------------------------------------------------------------
-// Stockham line FFT configuration per N.  E points per thread, T = N / E threads per line.
-// Stage k has sub-length Ns_k = E^k and radix R_k = min(E, N / Ns_k).
+// Stockham line FFT configuration.  E points per thread (default 16 for N <= 256, else 32; a kernel
+// may choose another power of two), T = N / E threads per line.  Stage k has sub-length
+// Ns_k = E^k and radix R_k = min(E, N / Ns_k).
 // ----------------------------------------------------------------------------------------------
-template <int N>
+template <int N, int EE = 0>
 struct FftCfg {
-    static constexpr int E = (N <= 256) ? 16 : 32;
+    static constexpr int E = EE ? EE : ((N <= 256) ? 16 : 32);
     static constexpr int T = N / E;
     static constexpr int stages = (N <= E) ? 1 : (N <= E * E ? 2 : 3);
     static constexpr int Ns(int k) { return k == 0 ? 1 : (k == 1 ? E : E * E); }
@@ -192,6 +193,9 @@ struct FftCfg {
     // offset of stage k's twiddles in the per-N table (stage 0 has none): sum (R_k' - 1) Ns_k'
     static constexpr int tw_off(int k) { return k <= 1 ? 0 : (Rk(1) - 1) * Ns(1) + (k <= 2 ? 0 : (Rk(2) - 1) * Ns(2)); }
     static constexpr int tw_size = tw_off(stages);
+    // twiddle table footprint in shared memory, rounded to 16 float2 so the line buffers after it keep
+    // the bank alignment the padding was designed for
+    static constexpr int tw_smem = ((tw_size > 0 ? tw_size : 1) + 15) / 16 * 16;
     // padded index inside one line's exchange buffer (in float2 units)
     __host__ __device__ static constexpr int pad(int x) { return x + x / E; }
     static constexpr int padded = N + N / E;
@@ -200,11 +204,9 @@ struct FftCfg {
 // One Stockham stage.  v[i] holds point t + i T on entry (stage input ordering).  Non-final
 // stages write to the line buffer `buf` (padded) and read back the next stage's inputs; `bar`
 // synchronises all threads sharing the buffer.
-template <int N, int K, int SIGN, class Bar>
-__device__ __forceinline__ void fft_stage(float2 (&v)[FftCfg<N>::E], float2* buf, int t, const float2* __restrict__ tw,
-                                          Bar bar)
+template <class C, int K, int SIGN, class Bar>
+__device__ __forceinline__ void fft_stage_c(float2 (&v)[C::E], float2* buf, int t, const float2* tw, Bar bar)
 {
-    using C = FftCfg<N>;
     constexpr int E = C::E, T = C::T;
     constexpr int R = C::Rk(K), Ns = C::Ns(K), B = E / R;
     constexpr bool LAST = (K == C::stages - 1);
@@ -216,7 +218,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[FftCfg<N>::E], float2* buf
             const float2* w = tw + C::tw_off(K) + jm;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const float2 wr = __ldg(w + (r - 1) * Ns);
+                const float2 wr = w[(r - 1) * Ns];
                 v[q + r * B] = SIGN < 0 ? cmul(v[q + r * B], wr) : cmulc(v[q + r * B], wr);
             }
         }
@@ -238,14 +240,31 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[FftCfg<N>::E], float2* buf
 }
 
 // Full length-N transform of one line: X[k] = sum_n x[n] exp(SIGN 2 pi i n k / N), unnormalised.
-template <int N, int SIGN, class Bar>
-__device__ __forceinline__ void line_fft(float2 (&v)[FftCfg<N>::E], float2* buf, int t, const float2* __restrict__ tw,
-                                         Bar bar)
+template <class C, int SIGN, class Bar>
+__device__ __forceinline__ void line_fft_c(float2 (&v)[C::E], float2* buf, int t, const float2* tw, Bar bar)
 {
-    using C = FftCfg<N>;
-    fft_stage<N, 0, SIGN>(v, buf, t, tw, bar);
-    if constexpr (C::stages > 1) fft_stage<N, 1, SIGN>(v, buf, t, tw, bar);
-    if constexpr (C::stages > 2) fft_stage<N, 2, SIGN>(v, buf, t, tw, bar);
+    fft_stage_c<C, 0, SIGN>(v, buf, t, tw, bar);
+    if constexpr (C::stages > 1) fft_stage_c<C, 1, SIGN>(v, buf, t, tw, bar);
+    if constexpr (C::stages > 2) fft_stage_c<C, 2, SIGN>(v, buf, t, tw, bar);
+}
+
+template <int N, int SIGN, class Bar>
+__device__ __forceinline__ void line_fft(float2 (&v)[FftCfg<N>::E], float2* buf, int t, const float2* tw, Bar bar)
+{
+    line_fft_c<FftCfg<N>, SIGN>(v, buf, t, tw, bar);
+}
+
+// Copies the stage twiddles into shared memory (all threads of the block; caller synchronises).
+template <class C>
+__device__ __forceinline__ void stage_twiddles_c(float2* dst, const float2* __restrict__ src)
+{
+    for (int i = threadIdx.x; i < C::tw_size; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+template <int N>
+__device__ __forceinline__ void stage_twiddles(float2* dst, const float2* __restrict__ src)
+{
+    stage_twiddles_c<FftCfg<N>>(dst, src);
 }
 
 struct WarpBar {

@@ -29,8 +29,12 @@ struct Plan {
     float src_coef[kMaxSources] = {};  // dx^2 / w0^2, or -1 for a plane wave
 
     // device tables (FP64-built, FP32-stored unless noted)
-    float2* tw = nullptr;      // Stockham stage twiddles, forward sign
-    float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N
+    float2* tw = nullptr;      // Stockham stage twiddles, forward sign (default E for N)
+    float2* tw16 = nullptr;    // the same for E = 16 (== tw when N <= 256)
+    int fft_e = 32;            // points per thread of the propagation passes (16 or 32; 16 for N <= 256)
+    float tune_us[2] = {0, 0}; // autotuner timings of one column + row pass for E = 16, 32 (0 = not run)
+    float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)
+    bool sep_transfer = false; // P includes the kappa^4 / 8k^3 term and kernels add the kx^2 ky^2 cross term
     float* dcoef = nullptr;    // [S] dz / (2 k^3)  (non-paraxial phase correction)
     float* amp = nullptr;      // [S] sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
     float* g = nullptr;        // [N][N] (kappa^2 + kappa0^2)^(-11/12) exp(-kappa^2 / 2 kappa_m^2), g(0) = 0
@@ -45,7 +49,7 @@ struct Plan {
     float* ws_shv = nullptr;      // [screen_chunk][7][N] subharmonic row vectors
     float* ws_shmean = nullptr;   // [screen_chunk] subharmonic piston
     double2* ws_sha = nullptr;    // [screen_chunk][27] subharmonic coefficients
-    float* ws_phi = nullptr;      // [max_batch][N][N] regenerated screens (phi == NULL paths)
+    float2* ws_phi = nullptr;     // [max_batch][N][N] regenerated screens as exp(i phi) (phi == NULL paths)
     double* ws_rows = nullptr;    // [max_batch][N][2] per-row beam sums
     size_t bytes = 0;
 
@@ -78,10 +82,12 @@ enum RowFlags : int {
     RP_OUT_FREQ = 8,
     RP_INTENSITY = 16,
     RP_STORE = 32,
+    RP_PHASOR = 64,  // modulation by precomputed exp(i phi) (complex64) instead of sincos(phi)
 };
 struct RowArgs {
     float2* field;
     const float* phi;          // screen s of set 0 (or nullptr)
+    const float2* phasor;      // exp(i phi) of screen s of set 0 (or nullptr)
     long long phi_set_stride;  // elements between screen sets
     int phi_group;
     float phase_sign;
@@ -108,7 +114,8 @@ struct ScreenArgs {
     double alpha_d, beta_d;
     float2* spec;              // AR state [items][N][N]
     double2* sh_state;         // AR subharmonic state [items][27]
-    float* phi;                // output [items][N][N]
+    float* phi;                // output [items][N][N] (or nullptr)
+    float2* phasor;            // output exp(i phi) [items][N][N] (or nullptr)
     bool tilt;
     double vx, vy, T;
 };

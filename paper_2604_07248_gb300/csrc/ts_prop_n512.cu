@@ -1,0 +1,8 @@
+// ts_prop_n512.cu -- propagation pass kernels for N = 512 (separate unit so the N variants compile in parallel).
+#include "ts_prop_impl.cuh"
+
+namespace ts {
+template cudaError_t row_pass_n<512>(int, int, const RowParams&, int, cudaStream_t);
+template cudaError_t col_pass_n<512>(int, bool, bool, const ColParams&, int, cudaStream_t);
+template cudaError_t prepare_prop_n<512>();
+}  // namespace ts

@@ -38,7 +38,7 @@ struct SColCfg {
     static constexpr int THREADS = 256;
     static constexpr int W = THREADS / C::T;
     static constexpr int LS = C::padded + (16 / W > 1 ? 16 / W : 1);
-    static constexpr size_t smem = sizeof(float2) * W * LS;
+    static constexpr size_t smem = sizeof(float2) * (C::tw_smem + W * LS);
 };
 
 template <int N, int MODE>
@@ -53,8 +53,10 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
     const int z = blockIdx.y;
     const int s = a.s_begin + z % a.s_count;
     const uint32_t r = a.r_begin + (uint32_t)(z / a.s_count);
-    float2* buf = smem + c * CC::LS;
+    float2* tw = smem;
+    float2* buf = smem + C::tw_smem + c * CC::LS;
     const float amp = __ldg(a.amp + s);
+    stage_twiddles<N>(tw, a.tw);
 
     float2 v[E];
     // bins (m, n) and (m + N/2, n) share one Philox call: registers i and i + E/2
@@ -84,7 +86,8 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
 #pragma unroll
         for (int i = 0; i < E; ++i) sp[(size_t)(t + i * T) * N] = v[i];
     }
-    line_fft<N, +1>(v, buf, t, a.tw, BlockBar());
+    __syncthreads();
+    line_fft<N, +1>(v, buf, t, tw, BlockBar());
     float2* yo = a.y + (size_t)z * N * N + n;
 #pragma unroll
     for (int i = 0; i < E; ++i) yo[(size_t)(t + i * T) * N] = v[i];
@@ -93,7 +96,8 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
 struct ScreenRowParams {
     const float2* tw;
     const float2* y;
-    float* phi;
+    float* phi;       // float32 screen, or nullptr
+    float2* phasor;   // exp(i phi), or nullptr
     const float* shv;      // [items][7][N]
     const float* shmean;   // [items]
     const float2* shy;     // [3][N]
@@ -105,7 +109,7 @@ struct SRowCfg {
     static constexpr int THREADS = 256;
     static constexpr int LPC = THREADS / C::T;
     static constexpr int LS = C::padded;
-    static constexpr size_t smem = sizeof(float2) * LPC * LS;
+    static constexpr size_t smem = sizeof(float2) * (C::tw_smem + LPC * LS);
 };
 
 template <int N, bool SH>
@@ -118,15 +122,19 @@ __global__ void __launch_bounds__(SRowCfg<N>::THREADS) screen_row_kernel(const S
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int j = blockIdx.x * RC::LPC + line;
     const int z = blockIdx.y;
-    float2* buf = smem + line * RC::LS;
+    float2* tw = smem;
+    float2* buf = smem + C::tw_smem + line * RC::LS;
     using Bar = typename std::conditional<(T > 32), BlockBar, WarpBar>::type;
 
     const float2* yrow = a.y + ((size_t)z * N + j) * N;
     float2 v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = yrow[t + i * T];
-    line_fft<N, +1>(v, buf, t, a.tw, Bar());
-    float* prow = a.phi + ((size_t)z * N + j) * N;
+    stage_twiddles<N>(tw, a.tw);
+    __syncthreads();
+    line_fft<N, +1>(v, buf, t, tw, Bar());
+    const size_t roff = ((size_t)z * N + j) * N;
+    // phi in v[i].x, then stored as requested: float32 screen and/or its phasor exp(i phi)
     if constexpr (SH) {
         const float* V = a.shv + (size_t)z * kShVectors * N;
         const float2 e1 = __ldg(a.shy + j), e2 = __ldg(a.shy + N + j), e3 = __ldg(a.shy + 2 * N + j);
@@ -141,11 +149,20 @@ __global__ void __launch_bounds__(SRowCfg<N>::THREADS) screen_row_kernel(const S
             sh = fmaf(e2.y, __ldg(V + 4 * N + x), sh);
             sh = fmaf(e3.x, __ldg(V + 5 * N + x), sh);
             sh = fmaf(e3.y, __ldg(V + 6 * N + x), sh);
-            prow[x] = v[i].x + sh;
+            v[i].x += sh;
         }
-    } else {
+    }
+    if (a.phi != nullptr) {
 #pragma unroll
-        for (int i = 0; i < E; ++i) prow[t + i * T] = v[i].x;
+        for (int i = 0; i < E; ++i) a.phi[roff + t + i * T] = v[i].x;
+    }
+    if (a.phasor != nullptr) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            float sn, cs;
+            sincosf(v[i].x, &sn, &cs);
+            a.phasor[roff + t + i * T] = make_float2(cs, sn);
+        }
     }
 }
 
@@ -314,7 +331,8 @@ cudaError_t screens_for(Plan& p, int mode, const ScreenArgs& a, cudaStream_t st)
         ScreenRowParams rp;
         rp.tw = p.tw;
         rp.y = p.ws_y;
-        rp.phi = a.phi + (size_t)z0 * N * N;
+        rp.phi = a.phi ? a.phi + (size_t)z0 * N * N : nullptr;
+        rp.phasor = a.phasor ? a.phasor + (size_t)z0 * N * N : nullptr;
         rp.shv = p.ws_shv;
         rp.shmean = p.ws_shmean;
         rp.shy = p.shy;
@@ -377,6 +395,7 @@ cudaError_t launch_screen_raw(int N, const float2* tw, const float* g, const flo
     rp.tw = tw;
     rp.y = y;
     rp.phi = phi;
+    rp.phasor = nullptr;
     cudaError_t e = cudaSuccess;
 #define TS_RAW(NN)                                                                                    \
     case NN: {                                                                                        \

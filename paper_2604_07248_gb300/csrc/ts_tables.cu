@@ -8,10 +8,9 @@ namespace ts {
 namespace {
 
 // Stockham stage twiddles exp(-2 pi i jm r / (Ns R)) for stages k >= 1 (forward sign).
-template <int N>
+template <class C>
 __global__ void twiddle_kernel(float2* tw)
 {
-    using C = FftCfg<N>;
     for (int k = 1; k < C::stages; ++k) {
         const int R = C::Rk(k), Ns = C::Ns(k);
         for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < (R - 1) * Ns; idx += gridDim.x * blockDim.x) {
@@ -23,13 +22,15 @@ __global__ void twiddle_kernel(float2* tw)
     }
 }
 
-// P[s][n] = exp(-i dz_s kappa_n^2 / 2k) / N  (paraxial factor of H, Sec. 2.4; 1/N per axis)
-__global__ void paraxial_kernel(float2* P, const double* dz, int S, int N, double dk, double k)
+// P[s][n] = exp(-i dz_s (kappa_n^2 / 2k [+ kappa_n^4 / 8k^3])) / N: the per-axis factors of H (Sec. 2.4;
+// 1/N per axis).  The quartic term is included when the kernels use the separable form.
+__global__ void paraxial_kernel(float2* P, const double* dz, int S, int N, double dk, double k, int quartic)
 {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S * N; idx += gridDim.x * blockDim.x) {
         const int s = idx / N, n = idx % N;
         const double kap = dk * (double)kidx(n, N);
-        const double ph = -dz[s] * kap * kap / (2.0 * k);
+        const double k2 = kap * kap;
+        const double ph = -dz[s] * (k2 / (2.0 * k) + (quartic ? k2 * k2 / (8.0 * k * k * k) : 0.0));
         double sn, cs;
         sincos(ph, &sn, &cs);
         P[idx] = make_float2((float)(cs / N), (float)(sn / N));
@@ -108,7 +109,14 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, uint32_t k0, uin
 template <int N>
 cudaError_t twiddles_for(float2* tw)
 {
-    twiddle_kernel<N><<<8, 256>>>(tw);
+    twiddle_kernel<FftCfg<N>><<<8, 256>>>(tw);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t twiddles16_for(float2* tw)
+{
+    twiddle_kernel<FftCfg<N, 16>><<<8, 256>>>(tw);
     return cudaGetLastError();
 }
 
@@ -126,13 +134,22 @@ cudaError_t build_tables(Plan& p)
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (p.tw16 != p.tw) {
+        switch (p.N) {
+        case 512: e = twiddles16_for<512>(p.tw16); break;
+        case 1024: e = twiddles16_for<1024>(p.tw16); break;
+        case 2048: e = twiddles16_for<2048>(p.tw16); break;
+        default: break;
+        }
+        if (e != cudaSuccess) return e;
+    }
 
     double* dz_d = nullptr;
     e = cudaMalloc(&dz_d, sizeof(double) * p.S);
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(dz_d, p.dz, sizeof(double) * p.S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        paraxial_kernel<<<64, 256>>>(p.P, dz_d, p.S, p.N, p.dk, p.k);
+        paraxial_kernel<<<64, 256>>>(p.P, dz_d, p.S, p.N, p.dk, p.k, p.sep_transfer ? 1 : 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -153,11 +170,11 @@ cudaError_t build_tables(Plan& p)
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st)
 {
     switch (N) {
-    case 128: twiddle_kernel<128><<<8, 256, 0, st>>>(tw); break;
-    case 256: twiddle_kernel<256><<<8, 256, 0, st>>>(tw); break;
-    case 512: twiddle_kernel<512><<<8, 256, 0, st>>>(tw); break;
-    case 1024: twiddle_kernel<1024><<<8, 256, 0, st>>>(tw); break;
-    case 2048: twiddle_kernel<2048><<<8, 256, 0, st>>>(tw); break;
+    case 128: twiddle_kernel<FftCfg<128>><<<8, 256, 0, st>>>(tw); break;
+    case 256: twiddle_kernel<FftCfg<256>><<<8, 256, 0, st>>>(tw); break;
+    case 512: twiddle_kernel<FftCfg<512>><<<8, 256, 0, st>>>(tw); break;
+    case 1024: twiddle_kernel<FftCfg<1024>><<<8, 256, 0, st>>>(tw); break;
+    case 2048: twiddle_kernel<FftCfg<2048>><<<8, 256, 0, st>>>(tw); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

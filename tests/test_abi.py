@@ -73,6 +73,6 @@ def test_status_strings_and_null_handling():
         assert lib.ts_status_string(s)
     assert lib.ts_plan_destroy(None) == 0
     assert lib.ts_plan_device_bytes(None) == 0
-    assert lib.ts_make_screens(None, 0, 0, 1, None, None) == 1
-    assert lib.ts_propagate(None, None, 1, None, 1, 0, 0, 0, None, None, None) == 1
+    assert lib.ts_make_screens(None, 0, 0, 1, None, None, None) == 1
+    assert lib.ts_propagate(None, None, 1, None, None, 1, 0, 0, 0, None, None, None) == 1
     assert b"need" in lib.ts_last_error()

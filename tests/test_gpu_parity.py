@@ -129,6 +129,44 @@ def test_propagate_with_given_screens_and_batches():
         assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
 
 
+def test_phasor_screens_give_the_same_fields_as_float_screens():
+    # exp(i phi) from the screen pass equals what the row pass would compute from phi: same results
+    N, dx, S, B = 256, 1e-3, 3, 4
+    plan = ts.Plan(LAM, N, dx, [100.0] * S, [2e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    plan.set_sources([0.02, 0.03])
+    phi = torch.zeros((2, S, N, N), dtype=torch.float32, device=DEV)
+    ph = torch.zeros((2, S, N, N), dtype=torch.complex64, device=DEV)
+    plan.make_screens(phi, 5, n_real=2, phasor=ph)
+    U1, U2, U3 = cfield(B, N), cfield(B, N), cfield(B, N)
+    plan.propagate(U1, B, phi=phi, phi_group=2, flags=ts.TS_PROP_SOURCE)
+    plan.propagate(U2, B, phasor=ph, phi_group=2, flags=ts.TS_PROP_SOURCE)
+    plan.propagate(U3, B, phi_group=2, flags=ts.TS_PROP_SOURCE, seed=5)  # regenerated from the seed
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2) and torch.equal(U2, U3)
+    g1, g2 = U1.clone(), U1.clone()
+    plan.propagate_backward(g1, B, phi=phi, phi_group=2)
+    plan.propagate_backward(g2, B, phasor=ph, phi_group=2)
+    torch.cuda.synchronize()
+    # the adjoint multiplies by conj(exp(i phi)) with a different FMA grouping than by exp(-i phi)
+    G1, G2 = g1.cpu().numpy(), g2.cpu().numpy()
+    assert np.linalg.norm(G1 - G2) / np.linalg.norm(G1) < 1e-6
+
+
+def test_exact_transfer_function_path():
+    # dx = 0.1 mm, N = 256, dz = 1.5 m: the kappa^6 term of the angular-spectrum phase reaches 7e-7 rad,
+    # so the plan keeps the exact (non-separable) transfer function.
+    N, dx, S = 256, 1e-4, 3
+    md = omedium(N, dx, l0=2e-4, L0=1.0)
+    plan = ts.Plan(LAM, N, dx, [1.5] * S, [1e-12] * S, l0=2e-4, L0=1.0, max_batch=1)
+    plan.set_sources([2e-3])
+    U = cfield(1, N)
+    plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE, seed=9)
+    torch.cuda.synchronize()
+    phis = np.stack([O.make_screen(md, 1e-12, 1.5, 0, 9, s, 0) for s in range(S)])
+    ref = O.propagate(md, [1.5] * S, phis, O.source_gaussian(N, dx, 2e-3))
+    assert rel_l2(U[0].cpu().numpy(), ref) < TOL, rel_l2(U[0].cpu().numpy(), ref)
+
+
 def test_ar_evolution_matches_oracle():
     # Eq. 4-5 with wind tilt, 4 steps, subharmonics on
     N, dx, S, alpha = 256, 1e-3, 3, 0.99
@@ -262,10 +300,11 @@ def test_config3_full_size_sampled_beams():
     plan.set_sources(w0)
     spec = torch.zeros((S, N, N), dtype=torch.complex64, device=DEV)
     phi = torch.zeros((S, N, N), dtype=torch.float32, device=DEV)
+    ph = torch.zeros((S, N, N), dtype=torch.complex64, device=DEV)
     U = cfield(8, N)
-    plan.evolve_screens(spec, phi, seed, 0, alpha)
-    plan.evolve_screens(spec, phi, seed, 1, alpha)
-    plan.propagate(U, 8, phi=phi, phi_group=8, flags=ts.TS_PROP_SOURCE)
+    plan.evolve_screens(spec, None, seed, 0, alpha, phasor=ph)
+    plan.evolve_screens(spec, phi, seed, 1, alpha, phasor=ph)
+    plan.propagate(U, 8, phasor=ph, phi_group=8, flags=ts.TS_PROP_SOURCE)
     torch.cuda.synchronize()
     md = omedium(N, dx)
     ref_phi = []
@@ -292,6 +331,28 @@ def test_large_grid_2048_and_energy():
     phis = np.stack([O.make_screen(md, 1e-15, 300.0, 0, 3, s, 0) for s in range(S)])
     ref = O.propagate(md, [300.0] * S, phis, O.source_gaussian(N, dx, 0.05))
     assert rel_l2(U[0].cpu().numpy(), ref) < TOL
+
+
+@pytest.mark.parametrize("E", [16, 32])
+def test_both_fft_variants_match_oracle(E, monkeypatch):
+    # the autotuner picks 16 or 32 points per thread; both variants must agree with the oracle
+    monkeypatch.setenv("TS_FFT_E", str(E))
+    N, dx, S = 1024, 5e-4, 3
+    plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
+    assert plan.tuning()[0] == E
+    plan.set_sources([0.01, 0.02])
+    U = cfield(2, N)
+    plan.propagate(U, 2, flags=ts.TS_PROP_SOURCE, seed=4)
+    g = U.clone()
+    plan.propagate_backward(g, 2, seed=4)
+    torch.cuda.synchronize()
+    md = omedium(N, dx)
+    phis = [np.stack([O.make_screen(md, 1e-14, 62.5, 0, 4, s, b) for s in range(S)]) for b in range(2)]
+    for b, w0 in enumerate((0.01, 0.02)):
+        ref = O.propagate(md, [62.5] * S, phis[b], O.source_gaussian(N, dx, w0))
+        assert rel_l2(U[b].cpu().numpy(), ref) < TOL
+        back = O.propagate_adjoint(md, [62.5] * S, phis[b], U[b].cpu().numpy())
+        assert rel_l2(g[b].cpu().numpy(), back) < TOL
 
 
 def test_errors_are_reported_not_launched():
