@@ -234,6 +234,44 @@ ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* tot
  * are device uint32 arrays of 4n words. */
 ts_status ts_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out, void* stream);
 
+/* ---------------------------------------------------------------------------------------------- */
+/* Uneven batches: independent instances of different grids and screen counts (Eq. 1 each),     */
+/* propagated by one persistent kernel launch.                                                    */
+/* ---------------------------------------------------------------------------------------------- */
+typedef struct ts_batch_s* ts_batch;
+
+typedef struct {
+    ts_plan plan;       /* the instance's medium, grid and path (kept alive by the caller)          */
+    void* field;        /* device complex64 [N][N]: input (unless source) and output                */
+    const void* phasor; /* device complex64 [S][N][N] screens as exp(i phi), or NULL: the batch
+                           synthesises them from (seed, real) exactly as ts_make_screens does      */
+    uint64_t seed;
+    uint32_t real;
+    int source;         /* nonzero: start from the plan's source 0 (ts_plan_set_sources)            */
+} ts_batch_instance;
+
+#define TS_BATCH_TEST_STALL 1 /* test hook: instance 0 waits for a tile that never completes, so its
+                                 dependency wait runs out and the batch reports TS_ERR_DEVICE_TIMEOUT */
+
+/* Builds a batch: validates the instances (all plans on the current device, separable transfer
+ * form), lays out the work list (instance, phase, tile) by increasing phase, allocates the screen
+ * workspace for instances without screens, and captures the run (screen synthesis, counter reset,
+ * one persistent launch) as a CUDA graph.  timeout_s bounds every device-side dependency wait.
+ * Copies `inst`; the plans, fields and screens must outlive the batch. */
+ts_status ts_batch_create(ts_batch* batch, const ts_batch_instance* inst, int n, double timeout_s, int flags);
+
+/* Launches the captured graph on `stream` (asynchronous). */
+ts_status ts_batch_run(ts_batch batch, void* stream);
+
+/* Synchronises `stream` and reads the batch's device error word: TS_OK, or TS_ERR_DEVICE_TIMEOUT if
+ * a dependency wait ran out (the kernel then stopped taking work; the CUDA context stays usable). */
+ts_status ts_batch_status(ts_batch batch, void* stream);
+
+/* Work items, persistent grid size (CTAs) and device bytes of the batch. */
+ts_status ts_batch_info(ts_batch batch, int* n_items, int* grid, size_t* device_bytes);
+
+ts_status ts_batch_destroy(ts_batch batch);
+
 const char* ts_status_string(ts_status status);
 
 /* One-line detail of the last error raised on the calling host thread ("" if none). */

@@ -32,6 +32,14 @@ class TsError(RuntimeError):
         self.status = status
 
 
+class BatchInstance(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("field", C.c_void_p), ("phasor", C.c_void_p), ("seed", C.c_uint64),
+                ("real", C.c_uint32), ("source", C.c_int)]
+
+
+TS_BATCH_TEST_STALL = 1
+
+
 class Medium(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("n0", C.c_double), ("l0", C.c_double), ("L0", C.c_double)]
 
@@ -66,6 +74,11 @@ SIGNATURES = {
     "ts_plan_timing": (_I, [_P, _I, _I]),
     "ts_plan_timing_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "ts_make_screen_noalloc": (_I, [C.POINTER(Medium), C.POINTER(Grid), _D, _D, _U64, _U32, _U32, _P, _P]),
+    "ts_batch_create": (_I, [C.POINTER(_P), C.POINTER(BatchInstance), _I, _D, _I]),
+    "ts_batch_run": (_I, [_P, _P]),
+    "ts_batch_status": (_I, [_P, _P]),
+    "ts_batch_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "ts_batch_destroy": (_I, [_P]),
     "ts_status_string": (C.c_char_p, [_I]),
     "ts_last_error": (C.c_char_p, []),
 }
@@ -240,3 +253,46 @@ class Plan:
         _check(load().ts_d2nn_backward(self._h, int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref), int(kind),
                                        _ptr(ws), _ptr(intensity), _ptr(g_th1), _ptr(g_th2), _ptr(gU),
                                        _stream(stream)), "ts_d2nn_backward")
+
+
+class Batch:
+    """Uneven batch of instances propagated by one persistent launch (ts_batch_*)."""
+
+    def __init__(self, instances, timeout_s=5.0, flags=0):
+        """instances: list of dicts with keys plan, field, phasor (or None), seed, real, source."""
+        arr = (BatchInstance * len(instances))()
+        for i, d in enumerate(instances):
+            arr[i].plan = d["plan"].handle.value
+            arr[i].field = _ptr(d["field"])
+            arr[i].phasor = _ptr(d.get("phasor"))
+            arr[i].seed = int(d.get("seed", 0))
+            arr[i].real = int(d.get("real", 0))
+            arr[i].source = 1 if d.get("source") else 0
+        self._keep = [d["plan"] for d in instances]
+        h = C.c_void_p()
+        _check(load().ts_batch_create(C.byref(h), arr, len(instances), float(timeout_s), int(flags)),
+               "ts_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(load().ts_batch_run(self._h, _stream(stream)), "ts_batch_run")
+
+    def status(self, stream=None) -> int:
+        """0, or the TS_ERR_* code the device reported (does not raise)."""
+        return load().ts_batch_status(self._h, _stream(stream))
+
+    def info(self):
+        n, g, b = C.c_int(), C.c_int(), C.c_size_t()
+        _check(load().ts_batch_info(self._h, C.byref(n), C.byref(g), C.byref(b)), "ts_batch_info")
+        return {"items": n.value, "grid": g.value, "device_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ts_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -31,22 +31,22 @@ struct RowCfg {
     static constexpr size_t smem = sizeof(float2) * (C::tw_smem + LPC * LS);
 };
 
-// at least two CTAs per SM (E = 32: <= 128 registers); E = 16 kernels fit four
+// One row tile: rows jblock * LPC .. + LPC - 1 of field b.  Shared by the per-pass kernel and the
+// persistent uneven-batch kernel; `smem` holds the twiddles (staged here when stage_tw) and the
+// per-line exchange buffers.
 template <int N, int EE, int FLAGS>
-__global__ void __launch_bounds__(kRowThreads, (FftCfg<N, EE>::E >= 32 ? 2 : 4)) row_pass_kernel(const RowParams a)
+__device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, float2* smem, bool stage_tw)
 {
     using C = FftCfg<N, EE>;
     using RC = RowCfg<N, EE>;
     constexpr int E = C::E, T = C::T;
-    extern __shared__ float2 smem[];
     const int line = threadIdx.x / T, t = threadIdx.x % T;
-    const int j = blockIdx.x * RC::LPC + line;
-    const int b = blockIdx.y;
+    const int j = jblock * RC::LPC + line;
     float2* tw = smem;
     float2* buf = smem + C::tw_smem + line * RC::LS;
     float2* row = a.field + ((size_t)b * N + j) * N;
     using Bar = typename std::conditional<(T > 32), BlockBar, WarpBar>::type;
-    stage_twiddles_c<C>(tw, a.tw);
+    if (stage_tw) stage_twiddles_c<C>(tw, a.tw);
     __syncthreads();
 
     float2 v[E];
@@ -116,6 +116,14 @@ __global__ void __launch_bounds__(kRowThreads, (FftCfg<N, EE>::E >= 32 ? 2 : 4))
     }
 }
 
+// at least two CTAs per SM (E = 32: <= 128 registers); E = 16 kernels fit four
+template <int N, int EE, int FLAGS>
+__global__ void __launch_bounds__(kRowThreads, (FftCfg<N, EE>::E >= 32 ? 2 : 4)) row_pass_kernel(const RowParams a)
+{
+    extern __shared__ float2 smem[];
+    row_tile<N, EE, FLAGS>(a, blockIdx.x, blockIdx.y, smem, true);
+}
+
 
 
 template <int N, int E>
@@ -153,24 +161,24 @@ __device__ __forceinline__ float2 small_phase(float e)
     return make_float2(1.0f - e2 * (0.5f - e2 * (1.0f / 24.0f)), -e * (1.0f - e2 * (1.0f / 6.0f)));
 }
 
+// One column tile: columns cblock * W .. + W - 1 of field b (see row_tile for smem).
 template <int N, int EE, bool CONJ, bool SEP>
-__global__ void __launch_bounds__(ColCfg<N, EE>::THREADS, 2) col_pass_kernel(const ColParams a)
+__device__ __forceinline__ void col_tile(const ColParams& a, int cblock, int b, float2* smem, bool stage_tw)
 {
     using C = FftCfg<N, EE>;
     using CC = ColCfg<N, EE>;
     constexpr int E = C::E, T = C::T, W = CC::W;
-    extern __shared__ float2 smem[];
     const int c = threadIdx.x % W, t = threadIdx.x / W;
-    const int col = blockIdx.x * W + c;
+    const int col = cblock * W + c;
     float2* tw = smem;
     float2* Ps = smem + C::tw_smem;
     float2* buf = Ps + N + c * CC::LS;
-    float2* base = a.field + (size_t)blockIdx.y * N * N + col;
+    float2* base = a.field + (size_t)b * N * N + col;
 
     float2 v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = base[(size_t)(t + i * T) * N];
-    stage_twiddles_c<C>(tw, a.tw);
+    if (stage_tw) stage_twiddles_c<C>(tw, a.tw);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Ps[i] = __ldg(a.P + i);
     __syncthreads();
     line_fft_c<C, -1>(v, buf, t, tw, BlockBar());
@@ -197,6 +205,13 @@ __global__ void __launch_bounds__(ColCfg<N, EE>::THREADS, 2) col_pass_kernel(con
     line_fft_c<C, +1>(v, buf, t, tw, BlockBar());
 #pragma unroll
     for (int i = 0; i < E; ++i) base[(size_t)(t + i * T) * N] = v[i];
+}
+
+template <int N, int EE, bool CONJ, bool SEP>
+__global__ void __launch_bounds__(ColCfg<N, EE>::THREADS, 2) col_pass_kernel(const ColParams a)
+{
+    extern __shared__ float2 smem[];
+    col_tile<N, EE, CONJ, SEP>(a, blockIdx.x, blockIdx.y, smem, true);
 }
 
 

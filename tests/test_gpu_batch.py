@@ -1,0 +1,111 @@
+"""Uneven batches (one persistent launch): equality with per-instance propagation, oracle parity,
+and the bounded dependency wait reporting a timeout without hanging the GPU."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2604_07248_gb300 as ts  # noqa: E402
+from paper_2604_07248_gb300 import workloads as W  # noqa: E402
+
+LAM = 1.55e-6
+DEV = torch.device("cuda:0")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+def make_instances(specs, seed):
+    plans, fields, insts = [], [], []
+    for i, (N, S, cn2) in enumerate(specs):
+        p = ts.Plan(LAM, N, 2e-3, [1000.0 / S] * S, [cn2] * S, l0=5e-3, L0=10.0, max_batch=1)
+        p.set_sources([0.02])
+        f = torch.zeros((N, N), dtype=torch.complex64, device=DEV)
+        plans.append(p)
+        fields.append(f)
+        insts.append(dict(plan=p, field=f, phasor=None, seed=seed, real=i, source=True))
+    return plans, fields, insts
+
+
+def test_batch_equals_per_instance_propagation(monkeypatch):
+    # per-instance passes with the same points per thread as the batch kernel: identical arithmetic
+    monkeypatch.setenv("TS_FFT_E", "32")
+    specs = [(256, 4, 1e-15), (512, 7, 3e-15), (1024, 5, 1e-14), (2048, 4, 1e-16), (512, 12, 1e-14),
+             (256, 20, 2e-16), (1024, 9, 5e-15)]
+    seed = W.SEED_BASE + 4
+    plans, fields, insts = make_instances(specs, seed)
+    batch = ts.Batch(insts, timeout_s=5.0)
+    batch.run()
+    assert batch.status() == 0
+    info = batch.info()
+    assert info["items"] == sum((2 * S + 1) * (N // (256 // (N // (16 if N <= 256 else 32))))
+                                for N, S, _ in specs)
+    for i, (N, S, cn2) in enumerate(specs):
+        ref = torch.zeros((1, N, N), dtype=torch.complex64, device=DEV)
+        plans[i].propagate(ref, 1, flags=ts.TS_PROP_SOURCE, seed=seed, real_base=i)
+        torch.cuda.synchronize()
+        assert torch.equal(fields[i], ref[0]), i
+    # a second run of the captured graph reproduces the result exactly
+    before = [f.clone() for f in fields]
+    batch.run()
+    assert batch.status() == 0
+    for f, g in zip(fields, before):
+        assert torch.equal(f, g)
+
+
+def test_batch_matches_oracle():
+    specs = [(256, 5, 1e-14), (512, 4, 3e-15)]
+    seed = 77
+    plans, fields, insts = make_instances(specs, seed)
+    batch = ts.Batch(insts)
+    batch.run()
+    assert batch.status() == 0
+    for i, (N, S, cn2) in enumerate(specs):
+        md = O.medium(LAM, N, 2e-3, l0=5e-3, L0=10.0)
+        dz = 1000.0 / S
+        phis = np.stack([O.make_screen(md, cn2, dz, 0, seed, s, i) for s in range(S)])
+        ref = O.propagate(md, [dz] * S, phis, O.source_gaussian(N, 2e-3, 0.02))
+        assert rel_l2(fields[i].cpu().numpy(), ref) < 1e-5
+
+
+def test_batch_with_given_screens_and_input_fields():
+    # caller-provided phasors and input fields (no source), shared by two instances of one plan
+    N, S = 512, 3
+    p = ts.Plan(LAM, N, 1e-3, [100.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
+    ph = torch.zeros((2, S, N, N), dtype=torch.complex64, device=DEV)
+    p.make_screens(None, 5, n_real=2, phasor=ph)
+    rng = np.random.default_rng(3)
+    U0 = (rng.standard_normal((2, N, N)) + 1j * rng.standard_normal((2, N, N))).astype(np.complex64)
+    fields = [torch.from_numpy(U0[b]).to(DEV) for b in range(2)]
+    insts = [dict(plan=p, field=fields[b], phasor=ph[b], source=False) for b in range(2)]
+    batch = ts.Batch(insts)
+    batch.run()
+    assert batch.status() == 0
+    ref = torch.from_numpy(U0).to(DEV)
+    p.propagate(ref, 2, phasor=ph, phi_group=1)
+    torch.cuda.synchronize()
+    for b in range(2):
+        assert rel_l2(fields[b].cpu().numpy(), ref[b].cpu().numpy()) < 1e-6
+
+
+def test_batch_dependency_wait_times_out_and_reports():
+    # the test hook makes instance 0 wait for a tile that never completes; the wait gives up after
+    # its budget, the kernel stops taking work and the host sees TS_ERR_DEVICE_TIMEOUT
+    plans, fields, insts = make_instances([(256, 3, 1e-15), (512, 3, 1e-15)], 5)
+    bad = ts.Batch(insts, timeout_s=0.05, flags=ts.TS_BATCH_TEST_STALL)
+    bad.run()
+    assert bad.status() == 5
+    bad.close()
+    # the context is still usable: the same instances run normally afterwards
+    good = ts.Batch(insts, timeout_s=5.0)
+    good.run()
+    assert good.status() == 0
+    x = torch.ones(4, device=DEV)
+    assert float((x * 2).sum().item()) == 8.0
