@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--workload", default="ar-evolution", choices=["ar-evolution", "uneven"],
+                    help="ar-evolution: the headline N=1024 workload; uneven: 64-instance persistent batch")
     return ap.parse_args()
 
 
@@ -395,10 +397,61 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_uneven(args):
+    """64 instances, N in {256, 512, 1024, 2048}, 4..20 screens, Cn^2 log-uniform in [1e-16, 1e-14]
+    (seeded), Gaussian w0 = 2 cm, dx = 2 mm, L = 1 km.  One step = one replay of the batch graph:
+    screen synthesis for every instance plus ONE persistent propagation launch over all of them."""
+    import torch
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = W.config4_instances()
+    plans, fields, insts = [], [], []
+    for i, d in enumerate(spec):
+        p = ts.Plan(W.LAMBDA, d["N"], d["dx"], [d["L"] / d["S"]] * d["S"], [d["cn2"]] * d["S"], l0=W.L0_INNER,
+                    L0=W.L0_OUTER, max_batch=1)
+        p.set_sources([d["w0"]])
+        f = torch.zeros((d["N"], d["N"]), dtype=torch.complex64, device=dev)
+        plans.append(p)
+        fields.append(f)
+        insts.append(dict(plan=p, field=f, phasor=None, seed=W.SEED_BASE + 4, real=rank * len(spec) + i,
+                          source=True))
+    batch = ts.Batch(insts, timeout_s=10.0)
+    units = sum(d["S"] for d in spec)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        batch.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = batch.status()
+    counts = {}
+    for d in spec:
+        counts[d["N"]] = counts.get(d["N"], 0) + 1
+    res = {"metric": "field·screen steps/s, uneven batch (one persistent launch per step)",
+           "value": round(args.steps * units * world / (ms * 1e-3), 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "uneven batch: 64 instances", "instances_by_N": counts,
+                      "field_screen_steps_per_step": units, "batch": batch.info(), "status": status}}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_gpu(args)
 

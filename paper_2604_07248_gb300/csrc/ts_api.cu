@@ -287,8 +287,8 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     auto ok = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
-    ok(dalloc(*p, &p->tw, N));
-    if (N >= 512) ok(dalloc(*p, &p->tw16, N));
+    ok(dalloc(*p, &p->tw, 4 * (size_t)N));  // padded per-thread twiddle rows (FftCfg::tw_size <= 4 N)
+    if (N >= 512) ok(dalloc(*p, &p->tw16, 4 * (size_t)N));
     else p->tw16 = p->tw;
     ok(dalloc(*p, &p->P, (size_t)S * N));
     ok(dalloc(*p, &p->amp, S));

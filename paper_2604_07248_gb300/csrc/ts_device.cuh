@@ -192,12 +192,19 @@ struct FftCfg {
     static constexpr int stages = (N <= E) ? 1 : (N <= E * E ? 2 : 3);
     static constexpr int Ns(int k) { return k == 0 ? 1 : (k == 1 ? E : E * E); }
     static constexpr int Rk(int k) { return (N / Ns(k)) < E ? (N / Ns(k)) : E; }
-    // offset of stage k's twiddles in the per-N table (stage 0 has none): sum (R_k' - 1) Ns_k'
-    static constexpr int tw_off(int k) { return k <= 1 ? 0 : (Rk(1) - 1) * Ns(1) + (k <= 2 ? 0 : (Rk(2) - 1) * Ns(2)); }
+    // Stage k >= 1 twiddles are stored per jm (= j mod Ns) as a row of RP(k) float2: entries r = 1..R-1
+    // at (r - 1), padded so that rows are 16-byte aligned and lanes with consecutive jm reading 16-byte
+    // pairs hit distinct bank groups (row stride = 4 mod 32 words).  offset of stage k = sum Ns_k' RP(k').
+    static constexpr int RP(int k) { return Rk(k) == 2 ? 1 : Rk(k) + 2; }  // radix 2: one twiddle, no pad
+    static constexpr int tw_off(int k)
+    {
+        return k <= 1 ? 0 : Ns(1) * RP(1) + (k <= 2 ? 0 : Ns(2) * RP(2));
+    }
     static constexpr int tw_size = tw_off(stages);
     // twiddle table footprint in shared memory, rounded to 16 float2 so the line buffers after it keep
     // the bank alignment the padding was designed for
     static constexpr int tw_smem = ((tw_size > 0 ? tw_size : 1) + 15) / 16 * 16;
+    static_assert(tw_size <= 4 * N, "twiddle tables are allocated with 4 N entries");
     // padded index inside one line's exchange buffer (in float2 units)
     __host__ __device__ static constexpr int pad(int x) { return x + x / E; }
     static constexpr int padded = N + N / E;
@@ -217,11 +224,21 @@ __device__ __forceinline__ void fft_stage_c(float2 (&v)[C::E], float2* buf, int 
         const int j = t + q * T;
         if constexpr (K > 0) {
             const int jm = j & (Ns - 1);
-            const float2* w = tw + C::tw_off(K) + jm;
+            if constexpr (R == 2) {
+                const float2 wa = tw[C::tw_off(K) + jm];
+                v[q + B] = SIGN < 0 ? cmul(v[q + B], wa) : cmulc(v[q + B], wa);
+            } else {
+            const float4* w4 = reinterpret_cast<const float4*>(tw + C::tw_off(K) + jm * C::RP(K));
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const float2 wr = w[(r - 1) * Ns];
-                v[q + r * B] = SIGN < 0 ? cmul(v[q + r * B], wr) : cmulc(v[q + r * B], wr);
+            for (int r = 1; r < R; r += 2) {
+                const float4 pr = w4[(r - 1) / 2];  // twiddles r and r + 1
+                const float2 wa = make_float2(pr.x, pr.y);
+                v[q + r * B] = SIGN < 0 ? cmul(v[q + r * B], wa) : cmulc(v[q + r * B], wa);
+                if (r + 1 < R) {
+                    const float2 wb = make_float2(pr.z, pr.w);
+                    v[q + (r + 1) * B] = SIGN < 0 ? cmul(v[q + (r + 1) * B], wb) : cmulc(v[q + (r + 1) * B], wb);
+                }
+            }
             }
         }
         dft_strided<R, SIGN, B>(v + q);
@@ -260,7 +277,9 @@ __device__ __forceinline__ void line_fft(float2 (&v)[FftCfg<N>::E], float2* buf,
 template <class C>
 __device__ __forceinline__ void stage_twiddles_c(float2* dst, const float2* __restrict__ src)
 {
-    for (int i = threadIdx.x; i < C::tw_size; i += blockDim.x) dst[i] = __ldg(src + i);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int i = threadIdx.x; i < (C::tw_size + 1) / 2; i += blockDim.x) d4[i] = __ldg(s4 + i);
 }
 
 template <int N>

@@ -27,8 +27,8 @@ constexpr size_t kAlign = 256;
 constexpr size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kOffY = 0;                                                               // float2 [N][N]
 constexpr size_t kOffG = kOffY + round_up(sizeof(float2) * kNoAllocMaxN * kNoAllocMaxN);  // float [N][N]
-constexpr size_t kOffTw = kOffG + round_up(sizeof(float) * kNoAllocMaxN * kNoAllocMaxN);  // float2 [N]
-constexpr size_t kOffAmp = kOffTw + round_up(sizeof(float2) * kNoAllocMaxN);              // float [64]
+constexpr size_t kOffTw = kOffG + round_up(sizeof(float) * kNoAllocMaxN * kNoAllocMaxN);  // float2 [4N]
+constexpr size_t kOffAmp = kOffTw + round_up(sizeof(float2) * 4 * kNoAllocMaxN);          // float [64]
 constexpr size_t kNoAllocBytes = kOffAmp + round_up(sizeof(float) * kMaxScreens);
 
 static __device__ __align__(256) unsigned char ts_noalloc_scratch[kNoAllocBytes];

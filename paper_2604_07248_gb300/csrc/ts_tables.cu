@@ -12,12 +12,16 @@ template <class C>
 __global__ void twiddle_kernel(float2* tw)
 {
     for (int k = 1; k < C::stages; ++k) {
-        const int R = C::Rk(k), Ns = C::Ns(k);
-        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < (R - 1) * Ns; idx += gridDim.x * blockDim.x) {
-            const int r = idx / Ns + 1, jm = idx % Ns;
-            double s, c;
-            sincospi(-2.0 * (double)jm * (double)r / (double)(Ns * R), &s, &c);
-            tw[C::tw_off(k) + idx] = make_float2((float)c, (float)s);
+        const int R = C::Rk(k), Ns = C::Ns(k), RP = C::RP(k);
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < RP * Ns; idx += gridDim.x * blockDim.x) {
+            const int jm = idx / RP, r = idx % RP + 1;
+            float2 w = make_float2(0.0f, 0.0f);  // padding entries
+            if (r < R) {
+                double s, c;
+                sincospi(-2.0 * (double)jm * (double)r / (double)(Ns * R), &s, &c);
+                w = make_float2((float)c, (float)s);
+            }
+            tw[C::tw_off(k) + idx] = w;
         }
     }
 }
