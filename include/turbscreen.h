@@ -19,9 +19,10 @@
  *     (allocated once in ts_plan_create).  No call other than ts_plan_create / ts_plan_destroy
  *     allocates or frees device memory.
  *   - all work is enqueued asynchronously on the given CUDA stream (a cudaStream_t passed as
- *     void*; NULL = legacy default stream).  Argument checks happen on the host before any launch;
- *     a failing check launches nothing.  One plan must not be used concurrently from two streams
- *     (it owns a single workspace).
+ *     void*; NULL = legacy default stream); a call may fan work out to the plan's own streams and
+ *     joins them back into the caller's stream before returning.  Argument checks happen on the
+ *     host before any launch; a failing check launches nothing.  One plan must not be used
+ *     concurrently from two host threads or two unordered streams (it owns one workspace).
  *   - on error a call returns a non-zero ts_status and ts_last_error() gives a one-line detail.
  */
 #ifndef TURBSCREEN_H
@@ -94,11 +95,16 @@ ts_status ts_plan_destroy(ts_plan plan);
 /* Device bytes held by the plan (tables + workspace). */
 size_t ts_plan_device_bytes(ts_plan plan);
 
-/* Autotuner result of the plan: the propagation passes run with `points_per_thread` FFT points
- * per thread (16 or 32); us_e16 / us_e32 (either may be NULL) receive the timed cost in microseconds
- * of one column + one row pass for each candidate (0 when not timed: N <= 256, a cached result, or
- * TS_FFT_E set in the environment). */
-ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32);
+/* Autotuner result of the plan (chosen once per device, N, batch and transfer form; cached):
+ *  - the propagation passes run with `points_per_thread` FFT points per thread (16 or 32); us_e16 /
+ *    us_e32 receive the timed cost in microseconds of one column + one row pass of each candidate;
+ *  - `streams` = number of field groups ts_propagate runs concurrently on the plan's own streams when
+ *    the screens are given (1, 2 or 4; forked from and joined back to the caller's stream);
+ *    us_streams[3] receives the timed cost for 1, 2 and 4 groups.
+ * Outputs other than points_per_thread may be NULL; a 0 timing means not timed (N <= 256, a cached
+ * result, or TS_FFT_E / TS_PROP_STREAMS set in the environment). */
+ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
+                         float* us_streams);
 
 /* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
  * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */
@@ -228,6 +234,13 @@ ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* t
  * `kind` and their summed device time in milliseconds. */
 ts_status ts_plan_timing(ts_plan plan, int enable, int capacity);
 ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* total_ms);
+
+/* Split-BF16 tensor-core 32-point DFT, the building block of the tensor-core DFT variant: for
+ * v < nvec, X[v][q] = sum_j x[v][j] exp(sign 2 pi i j q / 32), computed as a BF16 GEMM with FP32
+ * accumulation in tensor memory (tcgen05) from hi/lo BF16 splits of both factors
+ * (hi.hi + hi.lo + lo.hi, about 2^-16 relative error).  x, X: device complex64 [nvec][32].
+ * err: device int, set to nonzero if the wait for the MMAs ran out of timeout_s. */
+ts_status ts_tc_dft32(const void* x, void* X, int nvec, int sign, double timeout_s, int* err, void* stream);
 
 /* Raw Philox4x32-10 words (Salmon et al., SC'11) of n counters, for bit-exact checks of the noise
  * generator used by the screens: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key).  ctr and out

@@ -58,7 +58,8 @@ SIGNATURES = {
     "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
     "ts_plan_destroy": (_I, [_P]),
     "ts_plan_device_bytes": (C.c_size_t, [_P]),
-    "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                            C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_plan_set_sources": (_I, [_P, _I, _P]),
     "ts_make_sources": (_I, [_P, _P, _I, _P]),
@@ -71,6 +72,7 @@ SIGNATURES = {
     "ts_d2nn_forward": (_I, [_P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
     "ts_d2nn_backward": (_I, [_P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P, _P, _P]),
     "ts_philox4x32_10": (_I, [_P, _U32, _U32, _I, _P, _P]),
+    "ts_tc_dft32": (_I, [_P, _P, _I, _I, _D, _P, _P]),
     "ts_plan_timing": (_I, [_P, _I, _I]),
     "ts_plan_timing_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "ts_make_screen_noalloc": (_I, [C.POINTER(Medium), C.POINTER(Grid), _D, _D, _U64, _U32, _U32, _P, _P]),
@@ -152,6 +154,17 @@ def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0
            "ts_make_screen_noalloc")
 
 
+def tc_dft32(x, X, sign=-1, err=None, timeout_s=1.0, stream=None):
+    """Split-BF16 tensor-core 32-point DFTs of x [nvec, 32] complex64 into X (see ts_tc_dft32)."""
+    import torch
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    nvec = x.numel() // 32
+    _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), float(timeout_s), _ptr(err), _stream(stream)),
+           "ts_tc_dft32")
+    return err
+
+
 class Plan:
     """One medium + grid + path on the current CUDA device (ts_plan)."""
 
@@ -183,10 +196,11 @@ class Plan:
         return load().ts_plan_device_bytes(self._h)
 
     def tuning(self):
-        """(points per thread chosen for the propagation passes, us for E=16, us for E=32)."""
-        e, a, b = C.c_int(), C.c_float(), C.c_float()
-        _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b)), "ts_plan_tuning")
-        return e.value, a.value, b.value
+        """(points per thread, us for E=16, us for E=32, concurrent field groups, us for 1/2/4 groups)."""
+        e, a, b, g = C.c_int(), C.c_float(), C.c_float(), C.c_int()
+        us = (C.c_float * 3)()
+        _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b), C.byref(g), us), "ts_plan_tuning")
+        return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -84,6 +84,11 @@ cudaError_t timed(Plan& p, int kind, cudaStream_t st, F&& launch)
 void free_plan(Plan* p)
 {
     destroy_events(p);
+    for (int i = 0; i < 3; ++i) {
+        if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
+        if (p->join[i]) cudaEventDestroy(p->join[i]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
                     p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows,
                     p->tw16 != p->tw ? p->tw16 : nullptr};
@@ -107,6 +112,68 @@ ts_status regen_screen(Plan& p, uint64_t seed, uint32_t real_base, int G, int s,
     a.phi = nullptr;
     a.phasor = p.ws_phi;
     return cuda_check(timed(p, 2, st, [&] { return launch_screens(p, SC_INDEP, a, st); }), "screen synthesis");
+}
+
+int rows_per_line(const Plan& p)
+{
+    const int T = p.N / (p.N <= 256 ? 16 : p.fft_e);
+    return T > 32 ? T / 32 : 1;
+}
+
+// Eq. 1 over the plan's S steps for fields [b0, b0 + B) of the caller's batch U, on one stream.
+ts_status prop_range(Plan& p, float2* U, int b0, int B, const float* phi, const void* phasor, int phi_group, int flags,
+                     uint64_t seed, uint32_t real_base, float* intensity, double* rows, cudaStream_t st)
+{
+    const int N = p.N, S = p.S;
+    const size_t N2 = (size_t)N * N;
+    const int G = (B + phi_group - 1) / phi_group;
+    float2* Ur = U + (size_t)b0 * N2;
+    const size_t set0 = (size_t)(b0 / phi_group) * S * N2;  // first screen set of the range
+    RowArgs ra{};
+    ra.field = Ur;
+    ra.phi_group = phi_group;
+    ra.phase_sign = 1.0f;
+    ra.B = B;
+    ra.b0 = b0;
+    const int f0 = ((flags & TS_PROP_SOURCE) ? RP_IN_SOURCE : 0) | RP_OUT_FREQ | RP_STORE;
+    ts_status stt =
+        cuda_check(timed(p, 1, st, [&] { return launch_row_pass(p, f0, ra, st); }), "ts_propagate first row pass");
+    if (stt != TS_OK) return stt;
+    for (int s = 0; s < S; ++s) {
+        stt = cuda_check(timed(p, 0, st, [&] { return launch_col_pass(p, s, false, Ur, B, st); }),
+                         "ts_propagate column pass");
+        if (stt != TS_OK) return stt;
+        int rf = RP_IN_FREQ | RP_STORE;
+        ra.phi = nullptr;
+        ra.phasor = nullptr;
+        ra.phi_set_stride = (long long)S * N2;
+        if (phasor) {
+            ra.phasor = reinterpret_cast<const float2*>(phasor) + set0 + (size_t)s * N2;
+            rf |= RP_PHASOR;
+        } else if (phi) {
+            ra.phi = phi + set0 + (size_t)s * N2;
+            rf |= RP_PHASE;
+        } else {
+            // regenerated screens: one per screen set of this range, realizations real_base + set index
+            if ((stt = regen_screen(p, seed, real_base + (uint32_t)(b0 / phi_group), G, s, st)) != TS_OK) return stt;
+            ra.phasor = p.ws_phi;
+            ra.phi_set_stride = (long long)N2;
+            ra.b0 = b0 % phi_group;  // sets counted from this range's first set
+            rf |= RP_PHASOR;
+        }
+        if (s < S - 1) {
+            rf |= RP_OUT_FREQ;
+        } else if (flags & TS_PROP_INTENSITY) {
+            rf |= RP_INTENSITY;
+            if (flags & TS_PROP_NO_FIELD) rf &= ~RP_STORE;
+            ra.intensity = intensity + (size_t)b0 * N2;
+            ra.rows = rows ? rows + (size_t)b0 * N * rows_per_line(p) * 2 : nullptr;
+        }
+        stt = cuda_check(timed(p, 1, st, [&] { return launch_row_pass(p, rf, ra, st); }), "ts_propagate row pass");
+        ra.b0 = b0;
+        if (stt != TS_OK) return stt;
+    }
+    return TS_OK;
 }
 
 // Autotuner: for N >= 512 the propagation passes exist with E = 16 and E = 32 points per thread
@@ -182,6 +249,90 @@ ts_status autotune(Plan& p)
     p.fft_e = best_e;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best_e;
+    return TS_OK;
+}
+
+// Second autotuner stage: how many field groups to propagate concurrently (1, 2 or 4 streams), timed
+// as one column + one row pass of B_t workspace fields per candidate.  Cached like the first stage;
+// TS_PROP_STREAMS=1|2|4 forces a choice.
+std::map<std::tuple<int, int, int, int, int>, int> g_group_cache;
+
+ts_status autotune_groups(Plan& p)
+{
+    p.prop_groups = 1;
+    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
+    if (Bt < 2) return TS_OK;
+    if (const char* env = std::getenv("TS_PROP_STREAMS")) {
+        const int g = std::atoi(env);
+        if (g == 1 || g == 2 || g == 4) {
+            p.prop_groups = std::min(g, Bt);
+            return TS_OK;
+        }
+    }
+    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0, p.fft_e);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_group_cache.find(key);
+        if (it != g_group_cache.end()) {
+            p.prop_groups = it->second;
+            return TS_OK;
+        }
+    }
+    const size_t N2 = (size_t)p.N * p.N;
+    cudaError_t e = cudaMemset(p.ws_y, 0, sizeof(float2) * N2 * Bt);
+    if (e == cudaSuccess) e = cudaMemset(p.ws_phi, 0, sizeof(float2) * N2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int cand[3] = {1, 2, 4};
+    float best = 1e30f;
+    int best_g = 1;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        const int groups = cand[c];
+        if (groups > Bt) break;
+        auto once = [&]() {
+            cudaError_t x = cudaEventRecord(p.fork, nullptr);
+            for (int g = 1; g < groups && x == cudaSuccess; ++g) x = cudaStreamWaitEvent(p.aux[g - 1], p.fork, 0);
+            const int per = (Bt + groups - 1) / groups;
+            for (int g = 0; g < groups && x == cudaSuccess; ++g) {
+                const int b0 = g * per, bg = std::min(per, Bt - b0);
+                if (bg <= 0) break;
+                cudaStream_t st = g == 0 ? nullptr : p.aux[g - 1];
+                RowArgs ra{};
+                ra.field = p.ws_y + (size_t)b0 * N2;
+                ra.phasor = p.ws_phi;
+                ra.phi_group = Bt;
+                ra.phase_sign = 1.0f;
+                ra.B = bg;
+                ra.b0 = b0;
+                x = launch_col_pass(p, 0, false, ra.field, bg, st);
+                if (x == cudaSuccess) x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, st);
+            }
+            for (int g = 1; g < groups && x == cudaSuccess; ++g) {
+                x = cudaEventRecord(p.join[g - 1], p.aux[g - 1]);
+                if (x == cudaSuccess) x = cudaStreamWaitEvent(nullptr, p.join[g - 1], 0);
+            }
+            return x;
+        };
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = once();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = once();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        p.tune_group_us[c] = ms * 1000.0f / 5.0f;
+        if (e == cudaSuccess && p.tune_group_us[c] < best * 0.97f) {  // prefer fewer streams unless 3 % faster
+            best = p.tune_group_us[c];
+            best_g = groups;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (groups)");
+    p.prop_groups = best_g;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_group_cache[key] = best_g;
     return TS_OK;
 }
 
@@ -338,8 +489,19 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         free_plan(p);
         return st;
     }
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        ok(cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
+        ok(cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming));
+    }
+    ok(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    if (e != cudaSuccess) {
+        ts_status st = cuda_check(e, "ts_plan_create streams");
+        free_plan(p);
+        return st;
+    }
     {
         ts_status st = autotune(*p);
+        if (st == TS_OK) st = autotune_groups(*p);
         if (st != TS_OK) {
             free_plan(p);
             return st;
@@ -360,13 +522,17 @@ ts_status ts_plan_destroy(ts_plan plan)
 
 size_t ts_plan_device_bytes(ts_plan plan) { return plan ? reinterpret_cast<Plan*>(plan)->bytes : 0; }
 
-ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32)
+ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
+                         float* us_streams)
 {
     if (!plan || !points_per_thread) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning: need plan and output");
     Plan* p = reinterpret_cast<Plan*>(plan);
     *points_per_thread = p->fft_e;
     if (us_e16) *us_e16 = p->tune_us[0];
     if (us_e32) *us_e32 = p->tune_us[1];
+    if (streams) *streams = p->prop_groups;
+    if (us_streams)
+        for (int i = 0; i < 3; ++i) us_streams[i] = p->tune_group_us[i];
     return TS_OK;
 }
 
@@ -461,52 +627,32 @@ ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, const
     if ((flags & TS_PROP_NO_FIELD) && !(flags & TS_PROP_INTENSITY))
         return fail(TS_ERR_INVALID_ARG, "ts_propagate: TS_PROP_NO_FIELD needs TS_PROP_INTENSITY");
     cudaStream_t st = as_stream(stream);
-    const int N = p->N, S = p->S;
-    const size_t N2 = (size_t)N * N;
-    const int G = (B + phi_group - 1) / phi_group;
     float2* U = reinterpret_cast<float2*>(field);
-
-    RowArgs ra{};
-    ra.field = U;
-    ra.phi_group = phi_group;
-    ra.phase_sign = 1.0f;
-    ra.B = B;
-    ra.phi = nullptr;
-    const int f0 = ((flags & TS_PROP_SOURCE) ? RP_IN_SOURCE : 0) | RP_OUT_FREQ | RP_STORE;
-    ts_status stt =
-        cuda_check(timed(*p, 1, st, [&] { return launch_row_pass(*p, f0, ra, st); }), "ts_propagate first row pass");
-    if (stt != TS_OK) return stt;
-    for (int s = 0; s < S; ++s) {
-        stt = cuda_check(timed(*p, 0, st, [&] { return launch_col_pass(*p, s, false, U, B, st); }),
-                         "ts_propagate column pass");
-        if (stt != TS_OK) return stt;
-        int rf = RP_IN_FREQ | RP_STORE;
-        ra.phi = nullptr;
-        ra.phasor = nullptr;
-        ra.phi_set_stride = (long long)S * N2;
-        if (phasor) {
-            ra.phasor = reinterpret_cast<const float2*>(phasor) + (size_t)s * N2;
-            rf |= RP_PHASOR;
-        } else if (phi) {
-            ra.phi = phi + (size_t)s * N2;
-            rf |= RP_PHASE;
-        } else {
-            if ((stt = regen_screen(*p, seed, real_base, G, s, st)) != TS_OK) return stt;
-            ra.phasor = p->ws_phi;
-            ra.phi_set_stride = (long long)N2;
-            rf |= RP_PHASOR;
+    // With the screens given, the fields split into groups propagated concurrently on the plan's extra
+    // streams (fork / join through events, so the call stays asynchronous and capturable): one group's
+    // partial last waves overlap another's kernels.  Regenerated screens share one workspace: no split.
+    const int groups = (phi || phasor) ? std::min(p->prop_groups, B) : 1;
+    ts_status stt = TS_OK;
+    if (groups <= 1) {
+        stt = prop_range(*p, U, 0, B, phi, phasor, phi_group, flags, seed, real_base, intensity,
+                         beam_sums ? p->ws_rows : nullptr, st);
+    } else {
+        stt = cuda_check(cudaEventRecord(p->fork, st), "ts_propagate fork");
+        for (int g = 1; g < groups && stt == TS_OK; ++g)
+            stt = cuda_check(cudaStreamWaitEvent(p->aux[g - 1], p->fork, 0), "ts_propagate fork");
+        const int per = (B + groups - 1) / groups;
+        for (int g = 0; g < groups && stt == TS_OK; ++g) {
+            const int b0 = g * per, bg = std::min(per, B - b0);
+            if (bg <= 0) break;
+            stt = prop_range(*p, U, b0, bg, phi, phasor, phi_group, flags, seed, real_base, intensity,
+                             beam_sums ? p->ws_rows : nullptr, g == 0 ? st : p->aux[g - 1]);
         }
-        if (s < S - 1) {
-            rf |= RP_OUT_FREQ;
-        } else if (flags & TS_PROP_INTENSITY) {
-            rf |= RP_INTENSITY;
-            if (flags & TS_PROP_NO_FIELD) rf &= ~RP_STORE;
-            ra.intensity = intensity;
-            ra.rows = beam_sums ? p->ws_rows : nullptr;
+        for (int g = 1; g < groups && stt == TS_OK; ++g) {
+            stt = cuda_check(cudaEventRecord(p->join[g - 1], p->aux[g - 1]), "ts_propagate join");
+            if (stt == TS_OK) stt = cuda_check(cudaStreamWaitEvent(st, p->join[g - 1], 0), "ts_propagate join");
         }
-        stt = cuda_check(timed(*p, 1, st, [&] { return launch_row_pass(*p, rf, ra, st); }), "ts_propagate row pass");
-        if (stt != TS_OK) return stt;
     }
+    if (stt != TS_OK) return stt;
     if (beam_sums) return cuda_check(launch_row_sums(*p, p->ws_rows, B, beam_sums, st), "ts_propagate beam sums");
     return TS_OK;
 }

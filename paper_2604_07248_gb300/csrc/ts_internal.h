@@ -33,6 +33,10 @@ struct Plan {
     float2* tw16 = nullptr;    // the same for E = 16 (== tw when N <= 256)
     int fft_e = 32;            // points per thread of the propagation passes (16 or 32; 16 for N <= 256)
     float tune_us[2] = {0, 0}; // autotuner timings of one column + row pass for E = 16, 32 (0 = not run)
+    int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
+    float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)
     bool sep_transfer = false; // P includes the kappa^4 / 8k^3 term and kernels add the kx^2 ky^2 cross term
     float* dcoef = nullptr;    // [S] dz / (2 k^3)  (non-paraxial phase correction)
@@ -95,6 +99,7 @@ struct RowArgs {
     float* intensity;
     double* rows;              // [B][N][2]
     int B;
+    int b0;                    // index of this launch's first field in the caller's batch (sources, screen sets)
 };
 cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st);

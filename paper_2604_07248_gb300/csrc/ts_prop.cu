@@ -39,6 +39,8 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
     rp.phasor = a.phasor;
     rp.phi_set_stride = a.phi_set_stride;
     rp.phi_group = a.phi_group > 0 ? a.phi_group : 1;
+    rp.phi_off = a.b0 % rp.phi_group;
+    rp.src_off = a.b0;
     rp.phase_sign = a.phase_sign;
     rp.intensity = a.intensity;
     rp.rows = a.rows;

@@ -12,6 +12,8 @@ struct RowParams {
     const float2* phasor;
     long long phi_set_stride;
     int phi_group;
+    int phi_off;     // field b of this launch uses screen set (b + phi_off) / phi_group
+    int src_off;     // field b of this launch starts as source (b + src_off) mod n_src
     float phase_sign;
     float* intensity;
     double* rows;

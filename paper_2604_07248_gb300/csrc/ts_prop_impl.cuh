@@ -51,7 +51,7 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
 
     float2 v[E];
     if constexpr (FLAGS & RP_IN_SOURCE) {
-        const float coef = a.src_coef[b % a.n_src];
+        const float coef = a.src_coef[(b + a.src_off) % a.n_src];
         const float y = (float)(j - N / 2);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -65,7 +65,7 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
     if constexpr (FLAGS & RP_IN_FREQ) line_fft_c<C, +1>(v, buf, t, tw, Bar());
     if constexpr (FLAGS & RP_PHASOR) {
         // exp(i phi) precomputed once per screen: multiply (forward) or multiply by the conjugate (adjoint)
-        const float2* ph = a.phasor + (long long)(b / a.phi_group) * a.phi_set_stride + (size_t)j * N;
+        const float2* ph = a.phasor + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * N;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const float2 e = __ldg(ph + t + i * T);
@@ -73,7 +73,7 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
         }
     } else if constexpr (FLAGS & RP_PHASE) {
         if (a.phi != nullptr) {
-            const float* ph = a.phi + (long long)(b / a.phi_group) * a.phi_set_stride + (size_t)j * N;
+            const float* ph = a.phi + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * N;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 float s, c;

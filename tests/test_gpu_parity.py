@@ -355,6 +355,36 @@ def test_both_fft_variants_match_oracle(E, monkeypatch):
         assert rel_l2(g[b].cpu().numpy(), back) < TOL
 
 
+@pytest.mark.parametrize("groups", [2, 4])
+def test_concurrent_field_groups_match_one_stream(groups, monkeypatch):
+    # fields split into groups on the plan's own streams give the same bits as one stream, with
+    # screen sets shared by pairs of fields, per-field sources, intensities and beam sums
+    N, dx, S, B = 256, 1e-3, 3, 6
+    md = omedium(N, dx)
+    ph = torch.zeros((3, S, N, N), dtype=torch.complex64, device=DEV)
+    outs = []
+    for g in (1, groups):
+        monkeypatch.setenv("TS_PROP_STREAMS", str(g))
+        plan = ts.Plan(LAM, N, dx, [100.0] * S, [2e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+        assert plan.tuning()[3] == g
+        plan.set_sources([0.01, 0.02, 0.03, 0.0])
+        if g == 1:
+            plan.make_screens(None, 9, n_real=3, phasor=ph)
+        U = cfield(B, N)
+        I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+        sums = torch.zeros((B, 2), dtype=torch.float64, device=DEV)
+        plan.propagate(U, B, phasor=ph, phi_group=2, flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY, intensity=I,
+                       beam_sums=sums)
+        torch.cuda.synchronize()
+        outs.append((U.clone(), I.clone(), sums.clone()))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    # and field 5 (screen set 2, source 1) against the oracle
+    phis = np.stack([O.make_screen(md, 2e-14, 100.0, 0, 9, s, 2) for s in range(S)])
+    ref = O.propagate(md, [100.0] * S, phis, O.source_gaussian(N, dx, 0.02))
+    assert rel_l2(outs[1][0][5].cpu().numpy(), ref) < TOL
+
+
 def test_errors_are_reported_not_launched():
     plan = ts.Plan(LAM, 128, 2e-3, [200.0], [1e-15], max_batch=2)
     U = cfield(3, 128)
