@@ -76,6 +76,12 @@ typedef struct ts_plan_s* ts_plan;
 
 /* ts_plan_create flags */
 #define TS_PLAN_ALLOW_ALIASING 1 /* skip the Eq. 7 step-size check (caller accepts aliasing) */
+#define TS_PLAN_SPLIT_BF16 2     /* propagation passes (column and row passes of Eq. 1, forward and adjoint)
+                                    on the tensor cores: every line DFT is a 32 x 32 four-step DFT whose
+                                    stages are BF16 GEMMs with FP32 accumulation, each factor split into
+                                    BF16 hi + lo (products hi.hi + hi.lo + lo.hi, about 2^-16 relative
+                                    error per stage).  N = 1024 only (else TS_ERR_UNSUPPORTED).  Screens,
+                                    moments and the D2NN receiver stay FP32.  Not accepted by ts_batch. */
 
 /* Creates a plan for one medium, grid and path.  sh_levels is 0 or 3 (subharmonic levels, Eq. 2,
  * scale factor 3).  max_batch bounds the number of fields per ts_propagate / ts_propagate_backward
@@ -85,9 +91,16 @@ typedef struct ts_plan_s* ts_plan;
  * Errors: TS_ERR_INVALID_ARG (null pointers, N not supported, dx/lambda/dz <= 0, cn2 < 0,
  * sh_levels not 0/3, max_batch < 1), TS_ERR_ALIASING (some dz above the Eq. 7 limit
  * dz_max = (N dx / 2) sqrt(k^2 - kappa_max^2) / kappa_max with kappa_max = pi / dx, unless
- * TS_PLAN_ALLOW_ALIASING), TS_ERR_UNSUPPORTED (grid reaches the evanescent region), TS_ERR_CUDA. */
+ * TS_PLAN_ALLOW_ALIASING), TS_ERR_UNSUPPORTED (grid reaches the evanescent region, or
+ * TS_PLAN_SPLIT_BF16 with N != 1024), TS_ERR_CUDA. */
 ts_status ts_plan_create(ts_plan* plan, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
                          int sh_levels, int max_batch, int flags);
+
+/* Device status of a TS_PLAN_SPLIT_BF16 plan: waits for all work on the device, then returns
+ * TS_ERR_DEVICE_TIMEOUT (and clears the flag) if a wait of its tensor-core passes for their MMAs ran
+ * out of its one-second budget since the last call -- the pass then stopped early and its output is
+ * incomplete -- else TS_OK.  Plans without the flag always return TS_OK. */
+ts_status ts_plan_device_status(ts_plan plan);
 
 /* Frees the plan's device memory (synchronises the device).  NULL is accepted. */
 ts_status ts_plan_destroy(ts_plan plan);
@@ -239,8 +252,12 @@ ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* tot
  * v < nvec, X[v][q] = sum_j x[v][j] exp(sign 2 pi i j q / 32), computed as a BF16 GEMM with FP32
  * accumulation in tensor memory (tcgen05) from hi/lo BF16 splits of both factors
  * (hi.hi + hi.lo + lo.hi, about 2^-16 relative error).  x, X: device complex64 [nvec][32].
+ * layout selects how the data operand is staged in shared memory: 0 = K-major, 1 = MN-major (the
+ * form the tensor-core propagation passes use between their two DFT stages), 2 = MN-major with the
+ * two descriptor strides exchanged (a check of the descriptor reading; its result is not a DFT).
  * err: device int, set to nonzero if the wait for the MMAs ran out of timeout_s. */
-ts_status ts_tc_dft32(const void* x, void* X, int nvec, int sign, double timeout_s, int* err, void* stream);
+ts_status ts_tc_dft32(const void* x, void* X, int nvec, int sign, int layout, double timeout_s, int* err,
+                      void* stream);
 
 /* Raw Philox4x32-10 words (Salmon et al., SC'11) of n counters, for bit-exact checks of the noise
  * generator used by the screens: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key).  ctr and out

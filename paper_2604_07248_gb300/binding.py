@@ -21,6 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "aliasing (Eq. 7)", 3: "workspace",
           5: "device timeout", 6: "unsupported"}
 
 TS_PLAN_ALLOW_ALIASING = 1
+TS_PLAN_SPLIT_BF16 = 2
 TS_PROP_SOURCE = 1
 TS_PROP_INTENSITY = 2
 TS_PROP_NO_FIELD = 4
@@ -57,6 +58,7 @@ _P, _I, _D, _U32, _U64, _I64 = C.c_void_p, C.c_int, C.c_double, C.c_uint32, C.c_
 SIGNATURES = {
     "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
     "ts_plan_destroy": (_I, [_P]),
+    "ts_plan_device_status": (_I, [_P]),
     "ts_plan_device_bytes": (C.c_size_t, [_P]),
     "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
@@ -72,7 +74,7 @@ SIGNATURES = {
     "ts_d2nn_forward": (_I, [_P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
     "ts_d2nn_backward": (_I, [_P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P, _P, _P]),
     "ts_philox4x32_10": (_I, [_P, _U32, _U32, _I, _P, _P]),
-    "ts_tc_dft32": (_I, [_P, _P, _I, _I, _D, _P, _P]),
+    "ts_tc_dft32": (_I, [_P, _P, _I, _I, _I, _D, _P, _P]),
     "ts_plan_timing": (_I, [_P, _I, _I]),
     "ts_plan_timing_read": (_I, [_P, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "ts_make_screen_noalloc": (_I, [C.POINTER(Medium), C.POINTER(Grid), _D, _D, _U64, _U32, _U32, _P, _P]),
@@ -154,13 +156,14 @@ def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0
            "ts_make_screen_noalloc")
 
 
-def tc_dft32(x, X, sign=-1, err=None, timeout_s=1.0, stream=None):
+def tc_dft32(x, X, sign=-1, layout=0, err=None, timeout_s=1.0, stream=None):
     """Split-BF16 tensor-core 32-point DFTs of x [nvec, 32] complex64 into X (see ts_tc_dft32)."""
     import torch
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device=x.device)
     nvec = x.numel() // 32
-    _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), float(timeout_s), _ptr(err), _stream(stream)),
+    _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), int(layout), float(timeout_s), _ptr(err),
+                              _stream(stream)),
            "ts_tc_dft32")
     return err
 
@@ -201,6 +204,11 @@ class Plan:
         us = (C.c_float * 3)()
         _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b), C.byref(g), us), "ts_plan_tuning")
         return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]]
+
+    def device_status(self):
+        """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a tensor-core wait of a
+        TS_PLAN_SPLIT_BF16 plan ran out of its budget since the last call."""
+        _check(load().ts_plan_device_status(self._h), "ts_plan_device_status")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

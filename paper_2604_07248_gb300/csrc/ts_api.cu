@@ -91,7 +91,7 @@ void free_plan(Plan* p)
     if (p->fork) cudaEventDestroy(p->fork);
     void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
                     p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows,
-                    p->tw16 != p->tw ? p->tw16 : nullptr};
+                    p->tw16 != p->tw ? p->tw16 : nullptr, p->d_err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -186,6 +186,10 @@ std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 
 ts_status autotune(Plan& p)
 {
+    if (p.split_bf16) {
+        p.fft_e = 32;  // the tensor-core passes have one configuration
+        return TS_OK;
+    }
     if (p.N <= 256) {
         p.fft_e = 16;
         return TS_OK;
@@ -269,7 +273,7 @@ ts_status autotune_groups(Plan& p)
             return TS_OK;
         }
     }
-    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0, p.fft_e);
+    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0, p.split_bf16 ? -1 : p.fft_e);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_group_cache.find(key);
@@ -381,6 +385,8 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         return fail(TS_ERR_INVALID_ARG, "path needs 1..64 screens with dz and cn2 arrays");
     if (sh_levels != 0 && sh_levels != 3) return fail(TS_ERR_INVALID_ARG, "sh_levels must be 0 or 3");
     if (max_batch < 1) return fail(TS_ERR_INVALID_ARG, "max_batch must be >= 1");
+    if ((flags & TS_PLAN_SPLIT_BF16) && grid->N != 1024)
+        return fail(TS_ERR_UNSUPPORTED, "TS_PLAN_SPLIT_BF16 is implemented for N = 1024 (32 x 32 tensor-core DFTs)");
 
     Plan tmp;
     tmp.N = grid->N;
@@ -394,6 +400,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     tmp.L0 = medium->L0;
     tmp.k = wavenumber(medium);
     tmp.dk = 2.0 * M_PI / (grid->N * grid->dx);
+    tmp.split_bf16 = (flags & TS_PLAN_SPLIT_BF16) != 0;
     const double dzmax = ts_max_step(medium, grid);
     const double kap2max = 2.0 * std::pow(M_PI / grid->dx, 2.0);
     for (int s = 0; s < tmp.S; ++s) {
@@ -457,6 +464,13 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     ok(dalloc(*p, &p->ws_y, (size_t)p->screen_chunk * N2));
     ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * N2));  // regenerated screens as exp(i phi)
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
+    if (p->split_bf16) {
+        ok(dalloc(*p, &p->d_err, 1));
+        if (p->d_err) ok(cudaMemset(p->d_err, 0, sizeof(int)));
+        int khz = 0;
+        ok(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, p->device));
+        p->tc_budget = (long long)(1.0 * (double)(khz > 0 ? khz : 2000000) * 1e3);  // one second
+    }
     if (e != cudaSuccess) {
         ts_status st = cuda_check(e, "ts_plan_create allocation");
         free_plan(p);
@@ -482,6 +496,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     }
     ok(build_tables(*p));
     ok(prepare_prop_kernels(N));
+    if (p->split_bf16) ok(prepare_tc_prop());
     ok(prepare_screen_kernels(N));
     ok(prepare_d2nn_kernels(N));
     if (e != cudaSuccess) {
@@ -533,6 +548,20 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
     if (streams) *streams = p->prop_groups;
     if (us_streams)
         for (int i = 0; i < 3; ++i) us_streams[i] = p->tune_group_us[i];
+    return TS_OK;
+}
+
+ts_status ts_plan_device_status(ts_plan plan)
+{
+    if (!plan) return fail(TS_ERR_INVALID_ARG, "ts_plan_device_status: null plan");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!p->d_err) return TS_OK;
+    int code = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && code != 0) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(e, "ts_plan_device_status");
+    if (code != 0) return fail(TS_ERR_DEVICE_TIMEOUT, "a tensor-core wait of the plan ran out of its budget");
     return TS_OK;
 }
 

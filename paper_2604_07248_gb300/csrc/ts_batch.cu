@@ -267,6 +267,11 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
             free_batch(b);
             return bfail(TS_ERR_INVALID_ARG, "ts_batch_create: all plans must live on the current device");
         }
+        if (p->split_bf16) {
+            free_batch(b);
+            return bfail(TS_ERR_UNSUPPORTED, "ts_batch_create: instance " + std::to_string(i) +
+                                                 " uses the split-BF16 passes (the persistent batch kernel is FP32)");
+        }
         if (!p->sep_transfer) {
             free_batch(b);
             return bfail(TS_ERR_UNSUPPORTED, "ts_batch_create: instance " + std::to_string(i) +

@@ -32,6 +32,9 @@ struct Plan {
     float2* tw = nullptr;      // Stockham stage twiddles, forward sign (default E for N)
     float2* tw16 = nullptr;    // the same for E = 16 (== tw when N <= 256)
     int fft_e = 32;            // points per thread of the propagation passes (16 or 32; 16 for N <= 256)
+    bool split_bf16 = false;   // propagation passes on the tensor cores (split-BF16 DFTs, N = 1024)
+    int* d_err = nullptr;      // device error word of the tensor-core passes (nonzero after a timeout)
+    long long tc_budget = 0;   // clock64 cycles a tensor-core wait may take
     float tune_us[2] = {0, 0}; // autotuner timings of one column + row pass for E = 16, 32 (0 = not run)
     int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
@@ -102,6 +105,12 @@ struct RowArgs {
     int b0;                    // index of this launch's first field in the caller's batch (sources, screen sets)
 };
 cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStream_t st);
+// split-BF16 tensor-core passes (N = 1024), see ts_tc_prop.cu
+struct RowParams;
+struct ColParams;
+cudaError_t tc_row_pass(int flags, const RowParams& rp, int B, long long budget, int* err, cudaStream_t st);
+cudaError_t tc_col_pass(bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err, cudaStream_t st);
+cudaError_t prepare_tc_prop();
 cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st);
 cudaError_t prepare_prop_kernels(int N);
 cudaError_t prepare_screen_kernels(int N);

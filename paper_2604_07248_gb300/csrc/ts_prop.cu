@@ -48,6 +48,7 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
     rp.n_src = p.n_src > 0 ? p.n_src : 1;
     for (int i = 0; i < kMaxSources; ++i) rp.src_coef[i] = i < p.n_src ? p.src_coef[i] : -1.0f;
     rp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
+    if (p.split_bf16) return tc_row_pass(flags, rp, a.B, p.tc_budget, p.d_err, st);
     switch (p.N) {
     case 128: return row_pass_n<128>(p.fft_e, flags, rp, a.B, st);
     case 256: return row_pass_n<256>(p.fft_e, flags, rp, a.B, st);
@@ -69,6 +70,7 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
     cp.inv_k2 = (float)(1.0 / (p.k * p.k));
     cp.dk = (float)p.dk;
     cp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
+    if (p.split_bf16) return tc_col_pass(conj, p.sep_transfer, cp, B, p.tc_budget, p.d_err, st);
     switch (p.N) {
     case 128: return col_pass_n<128>(p.fft_e, conj, p.sep_transfer, cp, B, st);
     case 256: return col_pass_n<256>(p.fft_e, conj, p.sep_transfer, cp, B, st);

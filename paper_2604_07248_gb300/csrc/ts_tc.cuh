@@ -44,6 +44,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// MN-major, no swizzle: a core matrix is 8 columns k of 16 bytes (8 consecutive rows m each), 128
+// contiguous bytes.  The leading byte offset is the distance between groups of 8 columns k, the
+// stride byte offset the distance between core matrices adjacent along M / N (the reverse of the
+// K-major roles; checked on the GPU against an FP64 DFT with both assignments).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t k_group_stride, uint32_t mn_stride)
+{
+    return smem_desc(addr, k_group_stride, mn_stride);
+}
+
 // ---- instruction descriptor for kind::f16: BF16 x BF16 -> FP32, A and B K-major ----
 // c_format F32 = 1 at [4,6), a_format BF16 = 1 at [7,10), b_format BF16 = 1 at [10,13),
 // N >> 3 at [17,23), M >> 4 at [24,29).
@@ -51,6 +60,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// bit 15 of the instruction descriptor: A is MN-major (transposed) instead of K-major
+constexpr uint32_t kIdescTransposeA = 1u << 15;
 
 // D[tmem] (+)= A[smem] x B[smem]; one thread issues
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
@@ -111,6 +123,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16])
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+// 32 consecutive columns of this thread's TMEM lane into v[0..31].x (part 0) or .y (part 1); the
+// wait for the load is part of the same statement, so no register is read before it has arrived
+__device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, float2 (&v)[32], int part)
+{
+    if (part == 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=f"(v[0].x), "=f"(v[1].x), "=f"(v[2].x), "=f"(v[3].x), "=f"(v[4].x), "=f"(v[5].x), "=f"(v[6].x), "=f"(v[7].x), "=f"(v[8].x), "=f"(v[9].x), "=f"(v[10].x), "=f"(v[11].x), "=f"(v[12].x), "=f"(v[13].x), "=f"(v[14].x), "=f"(v[15].x), "=f"(v[16].x), "=f"(v[17].x), "=f"(v[18].x), "=f"(v[19].x), "=f"(v[20].x), "=f"(v[21].x), "=f"(v[22].x), "=f"(v[23].x), "=f"(v[24].x), "=f"(v[25].x), "=f"(v[26].x), "=f"(v[27].x), "=f"(v[28].x), "=f"(v[29].x), "=f"(v[30].x), "=f"(v[31].x)
+            : "r"(taddr)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=f"(v[0].y), "=f"(v[1].y), "=f"(v[2].y), "=f"(v[3].y), "=f"(v[4].y), "=f"(v[5].y), "=f"(v[6].y), "=f"(v[7].y), "=f"(v[8].y), "=f"(v[9].y), "=f"(v[10].y), "=f"(v[11].y), "=f"(v[12].y), "=f"(v[13].y), "=f"(v[14].y), "=f"(v[15].y), "=f"(v[16].y), "=f"(v[17].y), "=f"(v[18].y), "=f"(v[19].y), "=f"(v[20].y), "=f"(v[21].y), "=f"(v[22].y), "=f"(v[23].y), "=f"(v[24].y), "=f"(v[25].y), "=f"(v[26].y), "=f"(v[27].y), "=f"(v[28].y), "=f"(v[29].y), "=f"(v[30].y), "=f"(v[31].y)
+            : "r"(taddr)
+            : "memory");
+    }
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 

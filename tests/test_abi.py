@@ -57,13 +57,14 @@ def test_max_step_is_eq7_reading():
     (dict(sh_levels=2), 1),
     (dict(max_batch=0), 1),
     (dict(dz=[1000.0], cn2=[1e-15]), 2),  # above the Eq. 7 limit of 330 m at N = 128, dx = 2 mm
+    (dict(flags=bd.TS_PLAN_SPLIT_BF16), 6),  # the tensor-core passes exist for N = 1024 only
 ])
 def test_plan_rejects_bad_arguments_before_touching_the_gpu(kw, status):
-    args = dict(lam=1.55e-6, N=128, dx=2e-3, dz=[200.0], cn2=[1e-15], sh_levels=0, max_batch=1)
+    args = dict(lam=1.55e-6, N=128, dx=2e-3, dz=[200.0], cn2=[1e-15], sh_levels=0, max_batch=1, flags=0)
     args.update(kw)
     with pytest.raises(bd.TsError) as ei:
         bd.Plan(args["lam"], args["N"], args["dx"], args["dz"], args["cn2"], sh_levels=args["sh_levels"],
-                max_batch=args["max_batch"])
+                max_batch=args["max_batch"], flags=args["flags"])
     assert ei.value.status == status
 
 
@@ -73,6 +74,7 @@ def test_status_strings_and_null_handling():
         assert lib.ts_status_string(s)
     assert lib.ts_plan_destroy(None) == 0
     assert lib.ts_plan_device_bytes(None) == 0
+    assert lib.ts_plan_device_status(None) == 1
     assert lib.ts_make_screens(None, 0, 0, 1, None, None, None) == 1
     assert lib.ts_propagate(None, None, 1, None, None, 1, 0, 0, 0, None, None, None) == 1
     assert b"need" in lib.ts_last_error()
