@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--no-split-bf16", action="store_true",
+                    help="skip the split-BF16 tensor-core comparison (profiling runs)")
     ap.add_argument("--workload", default="ar-evolution", choices=["ar-evolution", "uneven"],
                     help="ar-evolution: the headline N=1024 workload; uneven: 64-instance persistent batch")
     return ap.parse_args()
@@ -173,11 +175,10 @@ def run_gpu(args):
     real = rank  # each rank evolves its own independent realization
     t_next = [0]
 
-    def step(src_from_field=False):
+    def step(p=plan):
         t = t_next[0]
-        plan.evolve_screens(spec, None, wl.seed, t, wl.alpha, real=real, phasor=phasor, stream=stream)
-        flags = 0 if src_from_field else ts.TS_PROP_SOURCE
-        plan.propagate(U, B, phasor=phasor, phi_group=B, flags=flags, stream=stream)
+        p.evolve_screens(spec, None, wl.seed, t, wl.alpha, real=real, phasor=phasor, stream=stream)
+        p.propagate(U, B, phasor=phasor, phi_group=B, flags=ts.TS_PROP_SOURCE, stream=stream)
         t_next[0] = t + 1
 
     def barrier():
@@ -304,6 +305,43 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(host_out[0].numel() * host_out[0].element_size()), "steps": n_e2e,
                "pipeline": "double-buffered fields, H2D and D2H on their own streams overlapping compute"}
 
+    # the same workload with the split-BF16 tensor-core passes (TS_PLAN_SPLIT_BF16): device-timed
+    # steps/s, and the per-frame rel-L2 of the 8 receiver fields against the FP32 passes through the
+    # same screens (the FP32 passes are themselves within 1e-5 of the FP64 oracle)
+    split = None
+    if not args.no_split_bf16:
+        tc_plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B,
+                          flags=ts.TS_PLAN_SPLIT_BF16)
+        tc_plan.set_sources(wl.w0)
+        U_fp = torch.zeros_like(U)
+        plan.propagate(U_fp, B, phasor=phasor, phi_group=B, flags=ts.TS_PROP_SOURCE, stream=stream)
+        tc_plan.propagate(U, B, phasor=phasor, phi_group=B, flags=ts.TS_PROP_SOURCE, stream=stream)
+        barrier()
+        tc_plan.device_status()
+        diff = (U.to(torch.complex128) - U_fp.to(torch.complex128)).abs().pow(2).sum(dim=(1, 2)).sqrt()
+        rel = (diff / U_fp.to(torch.complex128).abs().pow(2).sum(dim=(1, 2)).sqrt()).cpu().tolist()
+        del U_fp
+        n_tc = min(args.steps, 256)
+        for _ in range(args.warmup):
+            step(tc_plan)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(n_tc):
+            step(tc_plan)
+        g1.record(stream)
+        barrier()
+        tc_plan.device_status()
+        ms_tc = max_over_ranks(g0.elapsed_time(g1))
+        split = {"value": round(n_tc * B * S * world / (ms_tc * 1e-3), 1), "unit": UNIT, "steps": n_tc,
+                 "ms_per_step": round(ms_tc / n_tc, 5), "dtype": "bf16 hi+lo split, f32 accumulate",
+                 "rel_l2_vs_fp32_per_frame_max": float(f"{max(rel):.3e}"),
+                 "rel_l2_vs_fp32_per_frame": [float(f"{r:.3e}") for r in rel], "rel_l2_tolerance": 2e-3,
+                 "streams": tc_plan.tuning()[3],
+                 "note": "same workload and screens, AR update + 16 screens + 8 beams per step; column and "
+                         "row passes on tcgen05 (32 x 32 four-step DFT)"}
+        tc_plan.close()
+
     value = args.steps * B * S * world / (ms * 1e-3)
     res = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -318,6 +356,7 @@ def run_gpu(args):
                                          for x in plan.tuning()])),
                    "l2": "working set 320 MiB (AR spectra 128 + screen phasors 128 + fields 64) > 126 MB L2; no flush"},
         "roofline": roof,
+        "split_bf16": split,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
