@@ -134,19 +134,19 @@ def algorithmic_bytes(N, B, S):
 
 
 def load_traffic(kind_name):
-    """Per-launch DRAM bytes from the committed ncu summary, or None if the kernels changed since."""
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None when any source file
+    the kernel is built from changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        data = json.load(open(path))
+        k = json.load(open(path)).get("kernels", {}).get(kind_name)
     except (OSError, ValueError):
         return None
     from paper_2604_07248_gb300 import _build
-    if data.get("csrc_sha") != _build.source_sha():
+    if k is None or k.get("sources_sha") != _build.files_sha(k.get("sources", [])):
         return None
-    k = data.get("kernels", {}).get(kind_name)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    return k.get("dram_bytes_per_launch")
 
 
 def run_gpu(args):

@@ -38,6 +38,16 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+def files_sha(names) -> str:
+    """Hash of the named csrc files (identifies the sources one kernel is built from)."""
+    h = hashlib.sha256()
+    for n in sorted(names):
+        with open(os.path.join(CSRC, n), "rb") as fh:
+            h.update(n.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def source_sha() -> str:
     """Hash of the CUDA sources and the public header (identifies the kernels a profile was taken on)."""
     h = hashlib.sha256()

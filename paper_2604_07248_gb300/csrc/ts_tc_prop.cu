@@ -31,20 +31,23 @@ constexpr int kTN = 1024;
 constexpr int kPart = 16384;          // one 128 x 64 BF16 operand part (hi or lo)
 constexpr int kGroupA = 2 * kPart;    // hi + lo of one 128-vector group
 constexpr int kBPart = 8192;          // one 64 x 64 BF16 DFT-matrix part
-constexpr int kBBytes = 4 * kBPart;   // (sign -1, sign +1) x (hi, lo)
-constexpr int kTwBytes = 32 * 32 * 8; // exp(-2 pi i q l / 1024), [q][l]
+constexpr int kBBytes = 2 * kBPart;   // hi, lo of the forward 32-point DFT
+constexpr int kTwBytes = 31 * 32 * 8; // exp(-2 pi i q l / 1024), [q - 1][l], q = 1..31
 constexpr int kKRow = 1024;           // K-major: bytes between core matrices adjacent along M / N
 constexpr int kMnK = 2048;            // MN-major: bytes between groups of 8 columns k
+constexpr int kRowPerSm = 4;          // resident row-pass CTAs per SM (4 warps each)
+constexpr int kColPerSm = 2;          // resident column-pass CTAs per SM (8 warps each)
 
-// Shared memory layout (bytes): A operands of G groups, DFT matrices, twiddles, 32 cos / sin
-// values, mbarrier and TMEM address slot.
+// Shared memory layout (bytes): A operands of G groups, the split DFT matrix, twiddles, mbarrier
+// and TMEM address slot.  Only the forward DFT matrix is kept: an inverse transform is
+// conj(F conj(x)).  The cos / sin values the tables are built from live in the A area until the
+// first operand is written.
 template <int G>
 struct TcLayout {
     static constexpr int A = 0;
     static constexpr int B = G * kGroupA;
     static constexpr int TW = B + kBBytes;
-    static constexpr int CS = TW + kTwBytes;
-    static constexpr int BAR = CS + 32 * 8;
+    static constexpr int BAR = TW + kTwBytes;
     static constexpr int SIZE = BAR + 16;
 };
 
@@ -64,29 +67,28 @@ struct TcCtx {
     int* err;
 };
 
-// ---- tables staged per CTA: the split 32-point DFT matrices and the 1024-point twiddles ----
-template <int NT, int BOFF, int TWOFF, int CSOFF>
+// ---- tables staged per CTA: the split forward 32-point DFT matrix and the 1024-point twiddles ----
+template <int NT, int BOFF, int TWOFF>
 __device__ __forceinline__ void tc_build_tables(unsigned char* sm)
 {
-    float2* cs = reinterpret_cast<float2*>(sm + CSOFF);
+    float2* cs = reinterpret_cast<float2*>(sm);  // scratch in the A area
     if (threadIdx.x < 32) {
         float s, c;
         sincospif((float)threadIdx.x / 16.0f, &s, &c);  // exact arguments e / 16, e = 0..31
         cs[threadIdx.x] = make_float2(c, s);
     }
     float2* tw = reinterpret_cast<float2*>(sm + TWOFF);
-    for (int i = threadIdx.x; i < 1024; i += NT) {
-        const int q = i >> 5, l = i & 31;
+    for (int i = threadIdx.x; i < 31 * 32; i += NT) {
+        const int q = (i >> 5) + 1, l = i & 31;
         float s, c;
         sincospif((float)(q * l) / 512.0f, &s, &c);
         tw[i] = make_float2(c, -s);
     }
     __syncthreads();
-    // real form of the 32-point DFT with exponent sign sg, entry (input kk, output n):
+    // real form of the 32-point DFT with exponent sign -1, entry (input kk, output n):
     // kk, n < 32 are real parts, >= 32 imaginary parts; stored K-major (row n, column kk)
-    for (int task = threadIdx.x; task < 2 * 64 * 8; task += NT) {
-        const int si = task >> 9, n = (task >> 3) & 63, kc = task & 7;
-        const float sg = si == 0 ? -1.0f : 1.0f;
+    for (int task = threadIdx.x; task < 64 * 8; task += NT) {
+        const int n = task >> 3, kc = task & 7;
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -96,15 +98,20 @@ __device__ __forceinline__ void tc_build_tables(unsigned char* sm)
                 const int kk = 8 * kc + 2 * i + u;
                 const float2 e = cs[((kk & 31) * (n & 31)) & 31];
                 const bool im_in = kk >= 32, im_out = n >= 32;
-                g2[u] = (im_in == im_out) ? e.x : (im_out ? sg * e.y : -sg * e.y);
+                g2[u] = (im_in == im_out) ? e.x : (im_out ? -e.y : e.y);
             }
             tc::split_bf16x2(g2[0], g2[1], hi[i], lo[i]);
         }
         const uint32_t off = (uint32_t)((n >> 3) * kKRow + kc * 128 + (n & 7) * 16);
-        unsigned char* base = sm + BOFF + si * 2 * kBPart;
-        *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(base + kBPart + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<uint4*>(sm + BOFF + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sm + BOFF + kBPart + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+}
+
+__device__ __forceinline__ void conj32(float2 (&v)[32])
+{
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
 }
 
 // ---- operand staging ----
@@ -150,16 +157,16 @@ __device__ __forceinline__ void write_mnmajor(unsigned char* A, int g, int L, in
     }
 }
 
-// ---- one stage: all G groups, 12 MMAs each, then a bounded wait for their completion ----
+// ---- one stage: all G groups, 12 MMAs each (forward 32-point DFTs), then a bounded wait ----
 template <int G, int BOFF>
-__device__ __forceinline__ bool tc_stage(TcCtx& cx, bool mn, int sign)
+__device__ __forceinline__ bool tc_stage(TcCtx& cx, bool mn)
 {
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x == 0) {
-        const uint32_t a0 = tc::smem_u32(cx.sm), b0 = tc::smem_u32(cx.sm + BOFF) + (sign < 0 ? 0u : 2u * kBPart);
+        const uint32_t a0 = tc::smem_u32(cx.sm), b0 = tc::smem_u32(cx.sm + BOFF);
         const uint32_t idesc = tc::idesc_bf16_f32(128, 64) | (mn ? tc::kIdescTransposeA : 0u);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -195,19 +202,16 @@ __device__ __forceinline__ void tc_read(const TcCtx& cx, int g, float2 (&v)[32])
     tc::tmem_ld32_wait(addr + 32, v, 1);
 }
 
-// twiddle of stage a: v[q] *= exp(sign 2 pi i l q / 1024)
-__device__ __forceinline__ void tc_twiddle(const float2* tw, int l, int sign, float2 (&v)[32])
+// twiddle of stage a (forward transform): v[q] *= exp(-2 pi i l q / 1024)
+__device__ __forceinline__ void tc_twiddle(const float2* tw, int l, float2 (&v)[32])
 {
 #pragma unroll
-    for (int q = 1; q < 32; ++q) {
-        const float2 w = tw[q * 32 + l];
-        v[q] = sign < 0 ? cmul(v[q], w) : cmulc(v[q], w);
-    }
+    for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw[(q - 1) * 32 + l]);
 }
 
 // ---- row pass: 4 rows per tile (one warp per row, lane l holds elements l + 32 i) ----
 template <int FLAGS>
-__global__ void __launch_bounds__(128) tc_row_kernel(const RowParams a, const TcRun run)
+__global__ void __launch_bounds__(128, kRowPerSm) tc_row_kernel(const RowParams a, const TcRun run)
 {
     using Lay = TcLayout<1>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(128) tc_row_kernel(const RowParams a, const Tc
             tc::mbar_init(cx.bar, 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        tc_build_tables<128, Lay::B, Lay::TW, Lay::CS>(sm);
+        tc_build_tables<128, Lay::B, Lay::TW>(sm);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -248,14 +252,16 @@ __global__ void __launch_bounds__(128) tc_row_kernel(const RowParams a, const Tc
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = row[lane + 32 * i];
         }
-        if constexpr (FLAGS & RP_IN_FREQ) {
+        if constexpr (FLAGS & RP_IN_FREQ) {  // inverse transform: conj(F conj(v))
+            conj32(v);
             write_kmajor(sm, 0, threadIdx.x, v);
-            if (!(ok = tc_stage<1, Lay::B>(cx, false, +1))) break;
+            if (!(ok = tc_stage<1, Lay::B>(cx, false))) break;
             tc_read(cx, 0, v);
-            tc_twiddle(tw, lane, +1, v);
+            tc_twiddle(tw, lane, v);
             write_mnmajor(sm, 0, warp, lane, v);
-            if (!(ok = tc_stage<1, Lay::B>(cx, true, +1))) break;
+            if (!(ok = tc_stage<1, Lay::B>(cx, true))) break;
             tc_read(cx, 0, v);
+            conj32(v);
         }
         if constexpr (FLAGS & RP_PHASOR) {
             const float2* ph = a.phasor + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * kTN;
@@ -303,11 +309,11 @@ __global__ void __launch_bounds__(128) tc_row_kernel(const RowParams a, const Tc
         }
         if constexpr (FLAGS & RP_OUT_FREQ) {
             write_kmajor(sm, 0, threadIdx.x, v);
-            if (!(ok = tc_stage<1, Lay::B>(cx, false, -1))) break;
+            if (!(ok = tc_stage<1, Lay::B>(cx, false))) break;
             tc_read(cx, 0, v);
-            tc_twiddle(tw, lane, -1, v);
+            tc_twiddle(tw, lane, v);
             write_mnmajor(sm, 0, warp, lane, v);
-            if (!(ok = tc_stage<1, Lay::B>(cx, true, -1))) break;
+            if (!(ok = tc_stage<1, Lay::B>(cx, true))) break;
             tc_read(cx, 0, v);
         }
         if constexpr (FLAGS & RP_STORE) {
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(128) tc_row_kernel(const RowParams a, const Tc
 __device__ __forceinline__ uint32_t stage_off(int r, int c) { return (uint32_t)(r * 64 + ((c ^ ((r ^ (r >> 3)) & 7)) * 8)); }
 
 template <bool CONJ, bool SEP>
-__global__ void __launch_bounds__(256, 2) tc_col_kernel(const ColParams a, const TcRun run)
+__global__ void __launch_bounds__(256, kColPerSm) tc_col_kernel(const ColParams a, const TcRun run)
 {
     using Lay = TcLayout<2>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(256, 2) tc_col_kernel(const ColParams a, const
         tc::mbar_init(cx.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    tc_build_tables<256, Lay::B, Lay::TW, Lay::CS>(sm);
+    tc_build_tables<256, Lay::B, Lay::TW>(sm);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -363,11 +369,11 @@ __global__ void __launch_bounds__(256, 2) tc_col_kernel(const ColParams a, const
             for (int h = 0; h < 32; ++h) v[h] = base[(size_t)(32 * h + l) * kTN + c];
             // forward transform along the column
             write_kmajor(sm, g, m, v);
-            if (!(ok = tc_stage<2, Lay::B>(cx, false, -1))) break;
+            if (!(ok = tc_stage<2, Lay::B>(cx, false))) break;
             tc_read(cx, g, v);
-            tc_twiddle(tw, l, -1, v);
+            tc_twiddle(tw, l, v);
             write_mnmajor(sm, c >> 2, c & 3, l, v);
-            if (!(ok = tc_stage<2, Lay::B>(cx, true, -1))) break;
+            if (!(ok = tc_stage<2, Lay::B>(cx, true))) break;
             tc_read(cx, g, v);
         }
         // thread t: column col0 + (t >> 5), frequency (t & 31) + 32 i
@@ -404,14 +410,17 @@ __global__ void __launch_bounds__(256, 2) tc_col_kernel(const ColParams a, const
                 v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
             }
         }
-        // inverse transform: thread t's vector is (column t >> 5, k1 = t & 31) in group g, lane m
+        // inverse transform conj(F conj(v)): thread t's vector is (column t >> 5, k1 = t & 31) in
+        // group g, lane m
+        conj32(v);
         write_kmajor(sm, g, m, v);
-        if (!(ok = tc_stage<2, Lay::B>(cx, false, +1))) break;
+        if (!(ok = tc_stage<2, Lay::B>(cx, false))) break;
         tc_read(cx, g, v);
-        tc_twiddle(tw, k1, +1, v);
+        tc_twiddle(tw, k1, v);
         write_mnmajor(sm, warp >> 2, warp & 3, k1, v);
-        if (!(ok = tc_stage<2, Lay::B>(cx, true, +1))) break;
+        if (!(ok = tc_stage<2, Lay::B>(cx, true))) break;
         tc_read(cx, g, v);
+        conj32(v);
         // v[j1] = row k1 + 32 j1 of column col: stage through the (now free) operand area
 #pragma unroll
         for (int j1 = 0; j1 < 32; ++j1)
@@ -430,21 +439,21 @@ __global__ void __launch_bounds__(256, 2) tc_col_kernel(const ColParams a, const
     if (warp == 0) tc::tmem_dealloc(cx.tbase, 128);
 }
 
-static_assert(2 * (TcLayout<2>::SIZE + 1024) <= 228 * 1024, "two column-pass CTAs per SM");
-static_assert(3 * (TcLayout<1>::SIZE + 1024) <= 228 * 1024, "three row-pass CTAs per SM");
+static_assert(kColPerSm * (TcLayout<2>::SIZE + 1024) <= 228 * 1024, "column-pass CTAs per SM");
+static_assert(kRowPerSm * (TcLayout<1>::SIZE + 1024) <= 228 * 1024, "row-pass CTAs per SM");
+static_assert(kColPerSm * 128 + kRowPerSm * 64 <= 512, "TMEM columns of co-resident CTAs");
 static_assert(kTN * 8 * 8 <= 2 * kGroupA, "staging tile inside the operand area");
 
-// persistent grid: all CTAs that fit at once (cached per kernel), at most one per tile
-template <class K>
-int tc_grid(K kernel, int threads, int smem, int tiles, int& per_sm, int& sms)
+// persistent grid: the CTAs that are resident at once (per SM: the launch bounds' minimum, which the
+// register allocation and the shared-memory static_asserts above guarantee), at most one per tile
+int tc_grid(int per_sm, int tiles)
 {
-    if (per_sm < 0) {
-        int dev = 0, n = 0, bl = 0;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, kernel, threads, smem) != cudaSuccess || bl < 1) bl = 1;
         sms = n > 0 ? n : 1;
-        per_sm = bl;
     }
     const int g = per_sm * sms;
     return tiles < g ? tiles : g;
@@ -454,8 +463,7 @@ template <int FLAGS>
 cudaError_t tc_row_launch(const RowParams& rp, const TcRun& run, cudaStream_t st)
 {
     constexpr int smem = TcLayout<1>::SIZE;
-    static int per_sm = -1, sms = 0;
-    const int grid = tc_grid(tc_row_kernel<FLAGS>, 128, smem, run.tiles, per_sm, sms);
+    const int grid = tc_grid(kRowPerSm, run.tiles);
     tc_row_kernel<FLAGS><<<grid, 128, smem, st>>>(rp, run);
     return cudaGetLastError();
 }
@@ -464,8 +472,7 @@ template <bool CONJ, bool SEP>
 cudaError_t tc_col_launch(const ColParams& cp, const TcRun& run, cudaStream_t st)
 {
     constexpr int smem = TcLayout<2>::SIZE;
-    static int per_sm = -1, sms = 0;
-    const int grid = tc_grid(tc_col_kernel<CONJ, SEP>, 256, smem, run.tiles, per_sm, sms);
+    const int grid = tc_grid(kColPerSm, run.tiles);
     tc_col_kernel<CONJ, SEP><<<grid, 256, smem, st>>>(cp, run);
     return cudaGetLastError();
 }
