@@ -186,6 +186,7 @@ std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 
 ts_status autotune(Plan& p)
 {
+    p.col_variant = 0;
     if (p.split_bf16) {
         p.fft_e = 32;  // the tensor-core passes have one configuration
         return TS_OK;
@@ -194,21 +195,39 @@ ts_status autotune(Plan& p)
         p.fft_e = 16;
         return TS_OK;
     }
-    if (const char* env = std::getenv("TS_FFT_E")) {
-        const int e = std::atoi(env);
-        if (e == 16 || e == 32) {
-            p.fft_e = e;
-            return TS_OK;
+    // candidates (points per thread, column variant), filtered by TS_FFT_E / TS_COL_VARIANT
+    int force_e = 0, force_v = -1;
+    if (const char* env = std::getenv("TS_FFT_E")) force_e = std::atoi(env);
+    if (const char* env = std::getenv("TS_COL_VARIANT")) force_v = std::atoi(env);
+    const int cand_e[3] = {16, 32, 32}, cand_v[3] = {0, 0, 1};
+    bool use[3];
+    int n_use = 0, only = -1;
+    for (int c = 0; c < 3; ++c) {
+        use[c] = (force_e == 0 || force_e == cand_e[c]) && (force_v < 0 || force_v == cand_v[c]) &&
+                 (cand_v[c] == 0 || p.N == 1024);
+        if (use[c]) {
+            ++n_use;
+            only = c;
         }
+    }
+    if (n_use == 0) {  // an unavailable forced combination: keep the forced points per thread
+        p.fft_e = (force_e == 16 || force_e == 32) ? force_e : 32;
+        return TS_OK;
+    }
+    if (n_use == 1) {
+        p.fft_e = cand_e[only];
+        p.col_variant = cand_v[only];
+        return TS_OK;
     }
     const size_t N2 = (size_t)p.N * p.N;
     const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
-    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0);
+    const auto key = std::make_tuple(p.device, p.N, Bt, (p.sep_transfer ? 1 : 0) + 2 * (force_e + 64 * (force_v + 1)));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            p.fft_e = it->second;
+            p.fft_e = cand_e[it->second];
+            p.col_variant = cand_v[it->second];
             return TS_OK;
         }
     }
@@ -218,10 +237,11 @@ ts_status autotune(Plan& p)
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_e = 32;
-    const int cand[2] = {16, 32};
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
-        p.fft_e = cand[c];
+    int best_c = 1;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        if (!use[c]) continue;
+        p.fft_e = cand_e[c];
+        p.col_variant = cand_v[c];
         RowArgs ra{};
         ra.field = p.ws_y;
         ra.phasor = p.ws_phi;
@@ -244,15 +264,16 @@ ts_status autotune(Plan& p)
         p.tune_us[c] = ms * 1000.0f / 5.0f;
         if (e == cudaSuccess && p.tune_us[c] < best) {
             best = p.tune_us[c];
-            best_e = cand[c];
+            best_c = c;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune");
-    p.fft_e = best_e;
+    p.fft_e = cand_e[best_c];
+    p.col_variant = cand_v[best_c];
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = best_e;
+    g_tune_cache[key] = best_c;
     return TS_OK;
 }
 
@@ -273,7 +294,8 @@ ts_status autotune_groups(Plan& p)
             return TS_OK;
         }
     }
-    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0, p.split_bf16 ? -1 : p.fft_e);
+    const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0,
+                                     p.split_bf16 ? -1 : p.fft_e + 1000 * p.col_variant);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_group_cache.find(key);
@@ -470,6 +492,9 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         int khz = 0;
         ok(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, p->device));
         p->tc_budget = (long long)(1.0 * (double)(khz > 0 ? khz : 2000000) * 1e3);  // one second
+        // column tiles of 4 columns (one 128-vector group) unless TS_TC_COL_GROUPS=2 asks for 8
+        const char* env = std::getenv("TS_TC_COL_GROUPS");
+        p->tc_col_groups = (env && std::atoi(env) == 2) ? 2 : 1;
     }
     if (e != cudaSuccess) {
         ts_status st = cuda_check(e, "ts_plan_create allocation");
@@ -538,7 +563,7 @@ ts_status ts_plan_destroy(ts_plan plan)
 size_t ts_plan_device_bytes(ts_plan plan) { return plan ? reinterpret_cast<Plan*>(plan)->bytes : 0; }
 
 ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
-                         float* us_streams)
+                         float* us_streams, int* col_variant, float* us_e32_warp_columns)
 {
     if (!plan || !points_per_thread) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning: need plan and output");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -548,6 +573,8 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
     if (streams) *streams = p->prop_groups;
     if (us_streams)
         for (int i = 0; i < 3; ++i) us_streams[i] = p->tune_group_us[i];
+    if (col_variant) *col_variant = p->col_variant;
+    if (us_e32_warp_columns) *us_e32_warp_columns = p->tune_us[2];
     return TS_OK;
 }
 

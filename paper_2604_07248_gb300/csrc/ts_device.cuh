@@ -210,11 +210,18 @@ struct FftCfg {
     static constexpr int padded = N + N / E;
 };
 
+// Exchange storage of one line: element x at buf[pad(x)] (a padded per-line buffer).
+template <class C>
+struct PadMap {
+    float2* buf;
+    __device__ __forceinline__ float2* operator()(int x) const { return buf + C::pad(x); }
+};
+
 // One Stockham stage.  v[i] holds point t + i T on entry (stage input ordering).  Non-final
-// stages write to the line buffer `buf` (padded) and read back the next stage's inputs; `bar`
-// synchronises all threads sharing the buffer.
-template <class C, int K, int SIGN, class Bar>
-__device__ __forceinline__ void fft_stage_c(float2 (&v)[C::E], float2* buf, int t, const float2* tw, Bar bar)
+// stages write to the line's exchange storage (element x at map(x)) and read back the next stage's
+// inputs; `bar` synchronises all threads sharing the storage.
+template <class C, int K, int SIGN, class Bar, class Map>
+__device__ __forceinline__ void fft_stage_m(float2 (&v)[C::E], Map map, int t, const float2* tw, Bar bar)
 {
     constexpr int E = C::E, T = C::T;
     constexpr int R = C::Rk(K), Ns = C::Ns(K), B = E / R;
@@ -249,22 +256,34 @@ __device__ __forceinline__ void fft_stage_c(float2 (&v)[C::E], float2* buf, int 
             const int j = t + q * T;
             const int base = (j / Ns) * Ns * R + (j & (Ns - 1));
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[C::pad(base + r * Ns)] = v[q + r * B];
+            for (int r = 0; r < R; ++r) *map(base + r * Ns) = v[q + r * B];
         }
         bar();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = buf[C::pad(t + i * T)];
+        for (int i = 0; i < E; ++i) v[i] = *map(t + i * T);
         bar();
     }
 }
 
+template <class C, int K, int SIGN, class Bar>
+__device__ __forceinline__ void fft_stage_c(float2 (&v)[C::E], float2* buf, int t, const float2* tw, Bar bar)
+{
+    fft_stage_m<C, K, SIGN>(v, PadMap<C>{buf}, t, tw, bar);
+}
+
 // Full length-N transform of one line: X[k] = sum_n x[n] exp(SIGN 2 pi i n k / N), unnormalised.
+template <class C, int SIGN, class Bar, class Map>
+__device__ __forceinline__ void line_fft_m(float2 (&v)[C::E], Map map, int t, const float2* tw, Bar bar)
+{
+    fft_stage_m<C, 0, SIGN>(v, map, t, tw, bar);
+    if constexpr (C::stages > 1) fft_stage_m<C, 1, SIGN>(v, map, t, tw, bar);
+    if constexpr (C::stages > 2) fft_stage_m<C, 2, SIGN>(v, map, t, tw, bar);
+}
+
 template <class C, int SIGN, class Bar>
 __device__ __forceinline__ void line_fft_c(float2 (&v)[C::E], float2* buf, int t, const float2* tw, Bar bar)
 {
-    fft_stage_c<C, 0, SIGN>(v, buf, t, tw, bar);
-    if constexpr (C::stages > 1) fft_stage_c<C, 1, SIGN>(v, buf, t, tw, bar);
-    if constexpr (C::stages > 2) fft_stage_c<C, 2, SIGN>(v, buf, t, tw, bar);
+    line_fft_m<C, SIGN>(v, PadMap<C>{buf}, t, tw, bar);
 }
 
 template <int N, int SIGN, class Bar>

@@ -35,7 +35,9 @@ struct Plan {
     bool split_bf16 = false;   // propagation passes on the tensor cores (split-BF16 DFTs, N = 1024)
     int* d_err = nullptr;      // device error word of the tensor-core passes (nonzero after a timeout)
     long long tc_budget = 0;   // clock64 cycles a tensor-core wait may take
-    float tune_us[2] = {0, 0}; // autotuner timings of one column + row pass for E = 16, 32 (0 = not run)
+    int tc_col_groups = 1;     // tensor-core column tiles: 1 = 4 columns (4 CTAs / SM), 2 = 8 columns (2 CTAs / SM)
+    int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column (N = 1024, E = 32)
+    float tune_us[3] = {0, 0, 0};  // autotuner timings of one column + row pass: E = 16, E = 32, E = 32 warp columns
     int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
@@ -109,7 +111,8 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
 struct RowParams;
 struct ColParams;
 cudaError_t tc_row_pass(int flags, const RowParams& rp, int B, long long budget, int* err, cudaStream_t st);
-cudaError_t tc_col_pass(bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err, cudaStream_t st);
+cudaError_t tc_col_pass(int groups, bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err,
+                        cudaStream_t st);
 cudaError_t prepare_tc_prop();
 cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st);
 cudaError_t prepare_prop_kernels(int N);

@@ -70,13 +70,13 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
     cp.inv_k2 = (float)(1.0 / (p.k * p.k));
     cp.dk = (float)p.dk;
     cp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
-    if (p.split_bf16) return tc_col_pass(conj, p.sep_transfer, cp, B, p.tc_budget, p.d_err, st);
+    if (p.split_bf16) return tc_col_pass(p.tc_col_groups, conj, p.sep_transfer, cp, B, p.tc_budget, p.d_err, st);
     switch (p.N) {
-    case 128: return col_pass_n<128>(p.fft_e, conj, p.sep_transfer, cp, B, st);
-    case 256: return col_pass_n<256>(p.fft_e, conj, p.sep_transfer, cp, B, st);
-    case 512: return col_pass_n<512>(p.fft_e, conj, p.sep_transfer, cp, B, st);
-    case 1024: return col_pass_n<1024>(p.fft_e, conj, p.sep_transfer, cp, B, st);
-    case 2048: return col_pass_n<2048>(p.fft_e, conj, p.sep_transfer, cp, B, st);
+    case 128: return col_pass_n<128>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
+    case 256: return col_pass_n<256>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
+    case 512: return col_pass_n<512>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
+    case 1024: return col_pass_n<1024>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
+    case 2048: return col_pass_n<2048>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -35,8 +35,10 @@ struct ColParams {
 // Per-N entry points, instantiated in ts_prop_n<N>.cu (one translation unit per N builds in parallel).
 template <int N>
 cudaError_t row_pass_n(int E, int flags, const RowParams& rp, int B, cudaStream_t st);
+// variant 0: column lines shared by several warps (block synchronisation); variant 1 (N = 1024,
+// E = 32): one warp per column, tile staged through shared memory
 template <int N>
-cudaError_t col_pass_n(int E, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st);
+cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st);
 template <int N>
 cudaError_t prepare_prop_n();
 

@@ -161,6 +161,32 @@ __device__ __forceinline__ float2 small_phase(float e)
     return make_float2(1.0f - e2 * (0.5f - e2 * (1.0f / 24.0f)), -e * (1.0f - e2 * (1.0f / 6.0f)));
 }
 
+// v[i] (frequency t + i T of column col) *= H, or conj(H) for the adjoint; Ps = the step's P table
+template <int N, int E, bool CONJ, bool SEP>
+__device__ __forceinline__ void apply_transfer(float2 (&v)[E], const ColParams& a, const float2* Ps, int col, int t, int T)
+{
+    const float kx = a.dk * (float)kidx(col, N);
+    const float2 px = Ps[col];
+    if constexpr (SEP) {
+        const float cx = a.ccross * kx * kx;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + i * T;
+            const float ky = a.dk * (float)kidx(m, N);
+            const float2 h = cmul(cmul(px, Ps[m]), small_phase(cx * ky * ky));
+            v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + i * T;
+            const float ky = a.dk * (float)kidx(m, N);
+            const float2 h = transfer_exact(px, Ps[m], fmaf(kx, kx, ky * ky), a.inv_k2, a.dcoef);
+            v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+        }
+    }
+}
+
 // One column tile: columns cblock * W .. + W - 1 of field b (see row_tile for smem).
 template <int N, int EE, bool CONJ, bool SEP>
 __device__ __forceinline__ void col_tile(const ColParams& a, int cblock, int b, float2* smem, bool stage_tw)
@@ -182,29 +208,76 @@ __device__ __forceinline__ void col_tile(const ColParams& a, int cblock, int b, 
     for (int i = threadIdx.x; i < N; i += blockDim.x) Ps[i] = __ldg(a.P + i);
     __syncthreads();
     line_fft_c<C, -1>(v, buf, t, tw, BlockBar());
-    const float kx = a.dk * (float)kidx(col, N);
-    const float2 px = Ps[col];
-    if constexpr (SEP) {
-        const float cx = a.ccross * kx * kx;
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + i * T;
-            const float ky = a.dk * (float)kidx(m, N);
-            const float2 h = cmul(cmul(px, Ps[m]), small_phase(cx * ky * ky));
-            v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + i * T;
-            const float ky = a.dk * (float)kidx(m, N);
-            const float2 h = transfer_exact(px, Ps[m], fmaf(kx, kx, ky * ky), a.inv_k2, a.dcoef);
-            v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
-        }
-    }
+    apply_transfer<N, E, CONJ, SEP>(v, a, Ps, col, t, T);
     line_fft_c<C, +1>(v, buf, t, tw, BlockBar());
 #pragma unroll
     for (int i = 0; i < E; ++i) base[(size_t)(t + i * T) * N] = v[i];
+}
+
+// Warp-owned columns (N = 1024 with 32 points per thread, so one warp holds one column): the CTA
+// stages its 8-column tile through shared memory with coalesced loads, every warp then transforms
+// its own column using that column's part of the tile as its exchange storage (warp-level
+// synchronisation only, so warps progress independently), and the tile goes back with coalesced
+// stores.  Element x of column c sits in the 128-byte line pair y = x / 2 at 8-byte slot
+// ((x % 2) 8 + c) xor ((y xor y / 16) mod 16): the staging accesses, the Stockham stage-0 writes and
+// the strided reads all run at the 2-wavefront minimum.
+constexpr int kColWarpW = 8;
+
+__device__ __forceinline__ int tile_slot(int x, int c)
+{
+    const int y = x >> 1;
+    return y * 16 + ((((x & 1) << 3) + c) ^ ((y ^ (y >> 4)) & 15));
+}
+
+template <int N>
+struct ColWarpCfg {
+    using C = FftCfg<N, 32>;
+    static_assert(C::T == 32, "one warp per column");
+    static constexpr size_t smem = sizeof(float2) * (C::tw_smem + N + kColWarpW * N);
+};
+
+struct TileMap {
+    float2* tile;
+    int c;
+    __device__ __forceinline__ float2* operator()(int x) const { return tile + tile_slot(x, c); }
+};
+
+template <int N, bool CONJ, bool SEP>
+__global__ void __launch_bounds__(32 * kColWarpW, 2) col_pass_warp_kernel(const ColParams a)
+{
+    using C = typename ColWarpCfg<N>::C;
+    constexpr int E = C::E;
+    extern __shared__ float2 smem[];
+    float2* tw = smem;
+    float2* Ps = smem + C::tw_smem;
+    float2* tile = Ps + N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col0 = blockIdx.x * kColWarpW;
+    float2* base = a.field + (size_t)blockIdx.y * N * N + col0;
+    stage_twiddles_c<C>(tw, a.tw);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Ps[i] = __ldg(a.P + i);
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < kColWarpW * N; idx += blockDim.x) {
+        const int r = idx >> 3, c = idx & 7;
+        tile[tile_slot(r, c)] = base[(size_t)r * N + c];
+    }
+    __syncthreads();
+    const TileMap map{tile, warp};
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = *map(lane + 32 * i);
+    __syncwarp();  // every lane has its points before the exchange overwrites the column
+    line_fft_m<C, -1>(v, map, lane, tw, WarpBar());
+    apply_transfer<N, E, CONJ, SEP>(v, a, Ps, col0 + warp, lane, 32);
+    line_fft_m<C, +1>(v, map, lane, tw, WarpBar());
+#pragma unroll
+    for (int i = 0; i < E; ++i) *map(lane + 32 * i) = v[i];
+    __syncthreads();
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < kColWarpW * N; idx += blockDim.x) {
+        const int r = idx >> 3, c = idx & 7;
+        base[(size_t)r * N + c] = tile[tile_slot(r, c)];
+    }
 }
 
 template <int N, int EE, bool CONJ, bool SEP>
@@ -256,6 +329,14 @@ cudaError_t col_launch(const ColParams& cp, int B, cudaStream_t st)
     using CC = ColCfg<N, E>;
     dim3 grid(N / CC::W, B);
     col_pass_kernel<N, E, CONJ, SEP><<<grid, CC::THREADS, CC::smem, st>>>(cp);
+    return cudaGetLastError();
+}
+
+template <int N, bool CONJ, bool SEP>
+cudaError_t col_launch_warp(const ColParams& cp, int B, cudaStream_t st)
+{
+    dim3 grid(N / kColWarpW, B);
+    col_pass_warp_kernel<N, CONJ, SEP><<<grid, 32 * kColWarpW, ColWarpCfg<N>::smem, st>>>(cp);
     return cudaGetLastError();
 }
 
@@ -319,8 +400,14 @@ cudaError_t row_pass_n(int E, int flags, const RowParams& rp, int B, cudaStream_
 }
 
 template <int N>
-cudaError_t col_pass_n(int E, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st)
 {
+    if constexpr (N == 1024) {
+        if (variant == 1 && E == 32) {
+            if (sep) return conj ? col_launch_warp<N, true, true>(cp, B, st) : col_launch_warp<N, false, true>(cp, B, st);
+            return conj ? col_launch_warp<N, true, false>(cp, B, st) : col_launch_warp<N, false, false>(cp, B, st);
+        }
+    }
 #define TS_COLV(EE)                                                                                             \
     if (sep) return conj ? col_launch<N, EE, true, true>(cp, B, st) : col_launch<N, EE, false, true>(cp, B, st);  \
     return conj ? col_launch<N, EE, true, false>(cp, B, st) : col_launch<N, EE, false, false>(cp, B, st);
@@ -342,7 +429,15 @@ cudaError_t prepare_prop_n()
         return prepare_prop_for<N, 16>();
     } else {
         cudaError_t e = prepare_prop_for<N, 16>();
-        return e != cudaSuccess ? e : prepare_prop_for<N, 32>();
+        if (e == cudaSuccess) e = prepare_prop_for<N, 32>();
+        if constexpr (N == 1024) {
+            const int ws = (int)ColWarpCfg<N>::smem;
+            if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, false, false>, ws);
+            if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, true, false>, ws);
+            if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, false, true>, ws);
+            if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, true, true>, ws);
+        }
+        return e;
     }
 }
 

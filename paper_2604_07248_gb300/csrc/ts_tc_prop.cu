@@ -36,7 +36,8 @@ constexpr int kTwBytes = 31 * 32 * 8; // exp(-2 pi i q l / 1024), [q - 1][l], q 
 constexpr int kKRow = 1024;           // K-major: bytes between core matrices adjacent along M / N
 constexpr int kMnK = 2048;            // MN-major: bytes between groups of 8 columns k
 constexpr int kRowPerSm = 4;          // resident row-pass CTAs per SM (4 warps each)
-constexpr int kColPerSm = 2;          // resident column-pass CTAs per SM (8 warps each)
+constexpr int kColPerSm = 2;          // resident column-pass CTAs per SM, two groups (8 warps each)
+constexpr int kColPerSm1 = 4;         // resident column-pass CTAs per SM, one group (4 warps each)
 
 // Shared memory layout (bytes): A operands of G groups, the split DFT matrix, twiddles, mbarrier
 // and TMEM address slot.  Only the forward DFT matrix is kept: an inverse transform is
@@ -328,30 +329,40 @@ __global__ void __launch_bounds__(128, kRowPerSm) tc_row_kernel(const RowParams 
     }
 }
 
-// ---- column pass: 8 columns per tile, two 128-vector groups ----
-// Load map (coalesced, 64 bytes per row): thread t holds rows 32 h + (t >> 3) of column t & 7.
+// ---- column pass: W = 4 G columns per tile, G 128-vector groups ----
+// Load map (coalesced, 8 W bytes per row): thread t holds rows 32 h + t / W of column t % W.
 // After the forward transform thread t holds column t >> 5, frequencies (t & 31) + 32 k2; after
 // the inverse transform column t >> 5, rows (t & 31) + 32 j1, stored through a swizzled staging
-// tile in shared memory so that the global stores are coalesced again.
-__device__ __forceinline__ uint32_t stage_off(int r, int c) { return (uint32_t)(r * 64 + ((c ^ ((r ^ (r >> 3)) & 7)) * 8)); }
-
-template <bool CONJ, bool SEP>
-__global__ void __launch_bounds__(256, kColPerSm) tc_col_kernel(const ColParams a, const TcRun run)
+// tile in shared memory so that the global stores are coalesced again (both staging patterns run
+// at the 2-wavefront minimum).
+template <int W>
+__device__ __forceinline__ uint32_t stage_off(int r, int c)
 {
-    using Lay = TcLayout<2>;
+    if constexpr (W == 8) return (uint32_t)(r * 64 + ((c ^ ((r ^ (r >> 3)) & 7)) * 8));
+    else return (uint32_t)(r * 32 + ((c ^ ((r >> 2) & 3)) * 8));
+}
+
+template <int G>
+constexpr int tc_col_per_sm() { return G == 1 ? kColPerSm1 : kColPerSm; }
+
+template <int G, bool CONJ, bool SEP>
+__global__ void __launch_bounds__(128 * G, tc_col_per_sm<G>()) tc_col_kernel(const ColParams a, const TcRun run)
+{
+    using Lay = TcLayout<G>;
+    constexpr int W = 4 * G, NT = 128 * G;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int t = threadIdx.x, warp = t >> 5;
     TcCtx cx{sm, reinterpret_cast<uint64_t*>(sm + Lay::BAR), 0u, 0u, run.budget, run.err};
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Lay::BAR + 8);
     if (warp == 0) {
-        tc::tmem_alloc(tslot, 128);
+        tc::tmem_alloc(tslot, 64 * G);
         tc::tmem_relinquish();
     }
     if (t == 0) {
         tc::mbar_init(cx.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    tc_build_tables<256, Lay::B, Lay::TW>(sm);
+    tc_build_tables<NT, Lay::B, Lay::TW>(sm);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -360,20 +371,20 @@ __global__ void __launch_bounds__(256, kColPerSm) tc_col_kernel(const ColParams 
     const int g = t >> 7, m = t & 127;
     bool ok = true;
     for (int tile = blockIdx.x; tile < run.tiles && ok; tile += gridDim.x) {
-        const int b = tile >> 7, col0 = (tile & 127) << 3;
+        const int b = tile / (kTN / W), col0 = (tile % (kTN / W)) * W;
         float2* base = a.field + (size_t)b * kTN * kTN + col0;
         float2 v[32];
         {
-            const int l = t >> 3, c = t & 7;
+            const int l = t / W, c = t % W;
 #pragma unroll
             for (int h = 0; h < 32; ++h) v[h] = base[(size_t)(32 * h + l) * kTN + c];
             // forward transform along the column
             write_kmajor(sm, g, m, v);
-            if (!(ok = tc_stage<2, Lay::B>(cx, false))) break;
+            if (!(ok = tc_stage<G, Lay::B>(cx, false))) break;
             tc_read(cx, g, v);
             tc_twiddle(tw, l, v);
             write_mnmajor(sm, c >> 2, c & 3, l, v);
-            if (!(ok = tc_stage<2, Lay::B>(cx, true))) break;
+            if (!(ok = tc_stage<G, Lay::B>(cx, true))) break;
             tc_read(cx, g, v);
         }
         // thread t: column col0 + (t >> 5), frequency (t & 31) + 32 i
@@ -414,35 +425,36 @@ __global__ void __launch_bounds__(256, kColPerSm) tc_col_kernel(const ColParams 
         // group g, lane m
         conj32(v);
         write_kmajor(sm, g, m, v);
-        if (!(ok = tc_stage<2, Lay::B>(cx, false))) break;
+        if (!(ok = tc_stage<G, Lay::B>(cx, false))) break;
         tc_read(cx, g, v);
         tc_twiddle(tw, k1, v);
         write_mnmajor(sm, warp >> 2, warp & 3, k1, v);
-        if (!(ok = tc_stage<2, Lay::B>(cx, true))) break;
+        if (!(ok = tc_stage<G, Lay::B>(cx, true))) break;
         tc_read(cx, g, v);
         conj32(v);
         // v[j1] = row k1 + 32 j1 of column col: stage through the (now free) operand area
 #pragma unroll
         for (int j1 = 0; j1 < 32; ++j1)
-            *reinterpret_cast<float2*>(sm + stage_off(k1 + 32 * j1, warp)) = v[j1];
+            *reinterpret_cast<float2*>(sm + stage_off<W>(k1 + 32 * j1, warp)) = v[j1];
         __syncthreads();
 #pragma unroll 4
-        for (int idx = t; idx < kTN * 8; idx += 256) {
-            const int r = idx >> 3, c = idx & 7;
-            base[(size_t)r * kTN + c] = *reinterpret_cast<const float2*>(sm + stage_off(r, c));
+        for (int idx = t; idx < kTN * W; idx += NT) {
+            const int r = idx / W, c = idx % W;
+            base[(size_t)r * kTN + c] = *reinterpret_cast<const float2*>(sm + stage_off<W>(r, c));
         }
         // the next tile's operand writes reuse the staging area
         __syncthreads();
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(cx.tbase, 128);
+    if (warp == 0) tc::tmem_dealloc(cx.tbase, 64 * G);
 }
 
-static_assert(kColPerSm * (TcLayout<2>::SIZE + 1024) <= 228 * 1024, "column-pass CTAs per SM");
+static_assert(kColPerSm * (TcLayout<2>::SIZE + 1024) <= 228 * 1024, "column-pass CTAs per SM (two groups)");
+static_assert(kColPerSm1 * (TcLayout<1>::SIZE + 1024) <= 228 * 1024, "column-pass CTAs per SM (one group)");
 static_assert(kRowPerSm * (TcLayout<1>::SIZE + 1024) <= 228 * 1024, "row-pass CTAs per SM");
 static_assert(kColPerSm * 128 + kRowPerSm * 64 <= 512, "TMEM columns of co-resident CTAs");
-static_assert(kTN * 8 * 8 <= 2 * kGroupA, "staging tile inside the operand area");
+static_assert(kTN * 8 * 8 <= 2 * kGroupA && kTN * 4 * 8 <= kGroupA, "staging tile inside the operand area");
 
 // persistent grid: the CTAs that are resident at once (per SM: the launch bounds' minimum, which the
 // register allocation and the shared-memory static_asserts above guarantee), at most one per tile
@@ -468,12 +480,14 @@ cudaError_t tc_row_launch(const RowParams& rp, const TcRun& run, cudaStream_t st
     return cudaGetLastError();
 }
 
-template <bool CONJ, bool SEP>
-cudaError_t tc_col_launch(const ColParams& cp, const TcRun& run, cudaStream_t st)
+template <int G, bool CONJ, bool SEP>
+cudaError_t tc_col_launch(const ColParams& cp, int B, const TcRun& base, cudaStream_t st)
 {
-    constexpr int smem = TcLayout<2>::SIZE;
-    const int grid = tc_grid(kColPerSm, run.tiles);
-    tc_col_kernel<CONJ, SEP><<<grid, 256, smem, st>>>(cp, run);
+    constexpr int smem = TcLayout<G>::SIZE;
+    TcRun run = base;
+    run.tiles = B * (kTN / (4 * G));
+    const int grid = tc_grid(tc_col_per_sm<G>(), run.tiles);
+    tc_col_kernel<G, CONJ, SEP><<<grid, 128 * G, smem, st>>>(cp, run);
     return cudaGetLastError();
 }
 
@@ -487,13 +501,13 @@ cudaError_t tc_row_attr()
     return e;
 }
 
-template <bool CONJ, bool SEP>
+template <int G, bool CONJ, bool SEP>
 cudaError_t tc_col_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(tc_col_kernel<CONJ, SEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcLayout<2>::SIZE);
+    cudaError_t e = cudaFuncSetAttribute(tc_col_kernel<G, CONJ, SEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcLayout<G>::SIZE);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_col_kernel<CONJ, SEP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(tc_col_kernel<G, CONJ, SEP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 
@@ -527,11 +541,18 @@ cudaError_t tc_row_pass(int flags, const RowParams& rp, int B, long long budget,
     }
 }
 
-cudaError_t tc_col_pass(bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err, cudaStream_t st)
+cudaError_t tc_col_pass(int groups, bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err,
+                        cudaStream_t st)
 {
-    const TcRun run{B, B * (kTN / 8), budget, err};
-    if (sep) return conj ? tc_col_launch<true, true>(cp, run, st) : tc_col_launch<false, true>(cp, run, st);
-    return conj ? tc_col_launch<true, false>(cp, run, st) : tc_col_launch<false, false>(cp, run, st);
+    const TcRun run{B, 0, budget, err};
+#define TS_TC_COLG(G)                                                                                              \
+    if (sep) return conj ? tc_col_launch<G, true, true>(cp, B, run, st) : tc_col_launch<G, false, true>(cp, B, run, st); \
+    return conj ? tc_col_launch<G, true, false>(cp, B, run, st) : tc_col_launch<G, false, false>(cp, B, run, st);
+    if (groups == 2) {
+        TS_TC_COLG(2)
+    }
+    TS_TC_COLG(1)
+#undef TS_TC_COLG
 }
 
 cudaError_t prepare_tc_prop()
@@ -543,10 +564,14 @@ cudaError_t prepare_tc_prop()
 #define TS_TC_ATTR(F) chk(tc_row_attr<F>());
     TS_TC_ROW_FLAGS(TS_TC_ATTR)
 #undef TS_TC_ATTR
-    chk(tc_col_attr<false, false>());
-    chk(tc_col_attr<true, false>());
-    chk(tc_col_attr<false, true>());
-    chk(tc_col_attr<true, true>());
+    chk(tc_col_attr<1, false, false>());
+    chk(tc_col_attr<1, true, false>());
+    chk(tc_col_attr<1, false, true>());
+    chk(tc_col_attr<1, true, true>());
+    chk(tc_col_attr<2, false, false>());
+    chk(tc_col_attr<2, true, false>());
+    chk(tc_col_attr<2, false, true>());
+    chk(tc_col_attr<2, true, true>());
     return e;
 }
 

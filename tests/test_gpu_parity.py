@@ -152,6 +152,23 @@ def test_phasor_screens_give_the_same_fields_as_float_screens():
     assert np.linalg.norm(G1 - G2) / np.linalg.norm(G1) < 1e-6
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_exact_transfer_function_at_1024_both_column_variants(variant, monkeypatch):
+    # dx = 0.1 mm, dz = 2 m at N = 1024: the exact transfer function in both column-pass variants
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", str(variant))
+    N, dx, S = 1024, 1e-4, 2
+    md = omedium(N, dx, l0=2e-4, L0=1.0)
+    plan = ts.Plan(LAM, N, dx, [2.0] * S, [1e-12] * S, l0=2e-4, L0=1.0, max_batch=1)
+    plan.set_sources([2e-3])
+    U = cfield(1, N)
+    plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE, seed=13)
+    torch.cuda.synchronize()
+    phis = np.stack([O.make_screen(md, 1e-12, 2.0, 0, 13, s, 0) for s in range(S)])
+    ref = O.propagate(md, [2.0] * S, phis, O.source_gaussian(N, dx, 2e-3))
+    assert rel_l2(U[0].cpu().numpy(), ref) < TOL, rel_l2(U[0].cpu().numpy(), ref)
+
+
 def test_exact_transfer_function_path():
     # dx = 0.1 mm, N = 256, dz = 1.5 m: the kappa^6 term of the angular-spectrum phase reaches 7e-7 rad,
     # so the plan keeps the exact (non-separable) transfer function.
@@ -333,13 +350,16 @@ def test_large_grid_2048_and_energy():
     assert rel_l2(U[0].cpu().numpy(), ref) < TOL
 
 
-@pytest.mark.parametrize("E", [16, 32])
-def test_both_fft_variants_match_oracle(E, monkeypatch):
-    # the autotuner picks 16 or 32 points per thread; both variants must agree with the oracle
+@pytest.mark.parametrize("E,variant", [(16, 0), (32, 0), (32, 1)])
+def test_both_fft_variants_match_oracle(E, variant, monkeypatch):
+    # the autotuner picks 16 or 32 points per thread and, at 32, the column-pass variant (lines shared
+    # by four warps, or one warp per column with the tile staged in shared memory); every candidate
+    # must agree with the oracle, forward and adjoint
     monkeypatch.setenv("TS_FFT_E", str(E))
+    monkeypatch.setenv("TS_COL_VARIANT", str(variant))
     N, dx, S = 1024, 5e-4, 3
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
-    assert plan.tuning()[0] == E
+    assert plan.tuning()[0] == E and plan.tuning()[5] == variant
     plan.set_sources([0.01, 0.02])
     U = cfield(2, N)
     plan.propagate(U, 2, flags=ts.TS_PROP_SOURCE, seed=4)

@@ -90,6 +90,31 @@ def test_split_bf16_vacuum_gaussian_matches_analytic_beam():
     assert abs(np.sum(np.abs(got.astype(np.complex128)) ** 2) / e_in - 1) < 1e-4
 
 
+@pytest.mark.parametrize("groups", ["1", "2"])
+def test_split_bf16_column_tiles_of_4_and_8_columns(groups, monkeypatch):
+    # the column pass in tiles of 4 columns (one 128-vector group) or 8 (two groups): same result
+    # against the FP32 passes within the split-BF16 tolerance, both transfer directions
+    monkeypatch.setenv("TS_TC_COL_GROUPS", groups)
+    N, S, B = 1024, 3, 2
+    tc = ts.Plan(LAM, N, 5e-4, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B, flags=ts.TS_PLAN_SPLIT_BF16)
+    fp = ts.Plan(LAM, N, 5e-4, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    rng = np.random.default_rng(30)
+    U0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    out = []
+    for p in (tc, fp):
+        U = torch.from_numpy(U0).to(DEV)
+        p.propagate(U, B, seed=8)
+        g = torch.from_numpy(U0).to(DEV)
+        p.propagate_backward(g, B, seed=8)
+        torch.cuda.synchronize()
+        out.append((U.cpu().numpy(), g.cpu().numpy()))
+    tc.device_status()
+    for b in range(B):
+        for k in range(2):
+            r = rel_l2(out[0][k][b], out[1][k][b])
+            assert 1e-8 < r < TOL, (b, k, r)
+
+
 def test_split_bf16_exact_transfer_given_screens_and_adjoint():
     # dx = 0.1 mm, dz = 2 m: the kappa^6 term exceeds 1e-7 rad, so the exact transfer function runs;
     # float screens given, then the adjoint with screens regenerated from the seed
