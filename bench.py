@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--no-split-bf16", action="store_true",
                     help="skip the split-BF16 tensor-core comparison (profiling runs)")
-    ap.add_argument("--workload", default="ar-evolution", choices=["ar-evolution", "uneven"],
+    ap.add_argument("--workload", default="ar-evolution", choices=["ar-evolution", "uneven", "monte-carlo", "d2nn"],
                     help="ar-evolution: the headline N=1024 workload; uneven: 64-instance persistent batch")
     return ap.parse_args()
 
@@ -131,6 +131,32 @@ def algorithmic_bytes(N, B, S):
     row_avg = (row_first + S * row_mid) / (S + 1)
     screens = S * 40 * px + 4 * px
     return {0: col, 1: row_avg, 2: screens}
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline denominator: the measured copy bandwidth, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def propagate_bytes(N, B, S, shared_screen_fields, intensity_only=False):
+    """Algorithmic bytes of one ts_propagate call of B fields through S phasor screens, each screen
+    set shared by `shared_screen_fields` fields: first row pass writes the field (8 B/px); every
+    column pass reads + writes it (16); middle row passes read + write it (16) and read the phasor
+    once per set (8); the last row pass reads the field and the phasor and writes the field (or
+    only the 4-byte intensity)."""
+    px = N * N
+    sets = B / shared_screen_fields
+    last = (8 + 4) if intensity_only else (8 + 8)
+    return px * (8 * B + S * 16 * B + (S - 1) * 16 * B + last * B + S * 8 * sets)
+
+
+def screen_bytes(N, n_screens, ar=False):
+    """Algorithmic bytes of synthesising n_screens phasor screens: AR state read + write (16 B/px, AR
+    only), column-transformed spectrum write + read (16), phasor write (8), PSD shape read once."""
+    return N * N * (n_screens * ((16 if ar else 0) + 16 + 8) + 4)
 
 
 def load_traffic(kind_name):
@@ -350,7 +376,8 @@ def run_gpu(args):
         "config": {"workload": wl.name, "N": N, "dx": wl.dx, "L": wl.L, "screens": S, "beams": B,
                    "cn2": wl.cn2[0], "alpha": wl.alpha, "field_screen_steps_per_step": B * S,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "autotune": dict(zip(("points_per_thread", "us_e16", "us_e32", "streams", "us_streams_1_2_4"),
+                   "autotune": dict(zip(("points_per_thread", "us_e16", "us_e32", "streams", "us_streams_1_2_4",
+                                         "col_variant", "us_e32_warp_columns"),
                                         [round(x, 2) if isinstance(x, float) else
                                          ([round(y, 2) for y in x] if isinstance(x, list) else x)
                                          for x in plan.tuning()])),
@@ -493,12 +520,186 @@ def run_uneven(args):
     counts = {}
     for d in spec:
         counts[d["N"]] = counts.get(d["N"], 0) + 1
+    step_bytes = sum(screen_bytes(d["N"], d["S"]) + propagate_bytes(d["N"], 1, d["S"], 1) for d in spec)
+    peak, peak_src = hbm_peak()
+    gbs = step_bytes * world / (ms / args.steps * 1e-3) / 1e9
     res = {"metric": "field·screen steps/s, uneven batch (one persistent launch per step)",
            "value": round(args.steps * units * world / (ms * 1e-3), 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "uneven batch: 64 instances", "instances_by_N": counts,
-                      "field_screen_steps_per_step": units, "batch": batch.info(), "status": status}}
+                      "field_screen_steps_per_step": units, "batch": batch.info(), "status": status},
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
+                        "scope": "whole step (screen synthesis + the persistent launch), algorithmic bytes / time",
+                        "algorithmic_bytes_per_step": int(step_bytes)}}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def run_monte_carlo(args):
+    """Monte Carlo moments (N = 512, dx = 1 mm, L = 2 km, 10 screens with 3-level subharmonics, 8 Cn^2
+    values 10^(-16 + 3i/7)): one step = one chunk of 32 realizations for one Cn^2 (cycling through
+    the 8 values): synthesis of 32 x 10 screens (FFT part + subharmonics + piston), propagation of a
+    plane wave and a 2 cm Gaussian through each realization's screens (64 fields, intensity and beam
+    sums only), and the FP64 Welford merge of both groups' intensities.  Realization indices follow
+    i * 1000 + r."""
+    import torch
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cn2s = W.config2_cn2()
+    wl = W.config2(cn2s[0])
+    N, S, Rc = wl.N, wl.S, 32
+    B = 2 * Rc
+    plans = []
+    for c in cn2s:
+        p = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, [c] * S, l0=W.L0_INNER, L0=W.L0_OUTER, sh_levels=3, max_batch=B)
+        p.set_sources([0.0, 0.02])  # field 2r: plane wave, 2r + 1: Gaussian, both through screens r
+        plans.append(p)
+    ph = torch.zeros((Rc, S, N, N), dtype=torch.complex64, device=dev)
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=dev)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=dev)
+    sums = torch.zeros((B, 2), dtype=torch.float64, device=dev)
+    mean = torch.zeros((len(cn2s), 2, N, N), dtype=torch.float64, device=dev)
+    m2 = torch.zeros_like(mean)
+    count = [0] * len(cn2s)
+    chunk = [0] * len(cn2s)
+
+    def step(k):
+        i = k % len(cn2s)
+        p = plans[i]
+        r0 = rank * 100000 + i * 1000 + chunk[i] * Rc
+        p.make_screens(None, wl.seed, real_base=r0, n_real=Rc, phasor=ph)
+        p.propagate(U, B, phasor=ph, phi_group=2,
+                    flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY | ts.TS_PROP_NO_FIELD, intensity=I, beam_sums=sums)
+        p.moments_accumulate(I, B, 2, count[i], mean[i], m2[i])
+        count[i] += Rc
+        chunk[i] += 1
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    mean.zero_()
+    m2.zero_()
+    count = [0] * len(cn2s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    si = {}
+    for i, c in enumerate(cn2s):
+        if count[i] == 0:
+            continue
+        sm = torch.zeros(2, dtype=torch.float64, device=dev)
+        plans[i].moments_finalize(mean[i], m2[i], 2, count[i], si_mean=sm)
+        sig_r2 = 1.23 * c * (2 * 3.141592653589793 / W.LAMBDA) ** (7 / 6) * wl.L ** (11 / 6)
+        si[f"{c:.3g}"] = {"realizations": count[i], "sigma_R2": round(sig_r2, 4),
+                          "SI_plane_grid_mean": round(float(sm[0].item()), 4)}
+    units = args.steps * B * S * world
+    step_bytes = (screen_bytes(N, Rc * S) + propagate_bytes(N, B, S, 2, intensity_only=True)
+                  + N * N * (4 * B + 2 * 32))  # moments: intensities read, FP64 mean + M2 read + write
+    peak, peak_src = hbm_peak()
+    gbs = step_bytes / (ms / args.steps * 1e-3) / 1e9
+    res = {"metric": "field·screen steps/s, Monte Carlo moments (screens with subharmonics, 2 sources, Welford)",
+           "value": round(units / (ms * 1e-3), 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (moments f64)", "data": "synthetic",
+           "config": {"workload": "monte-carlo N=512 S=10 SH3, 8 Cn2, plane + Gaussian 2 cm", "N": N, "dx": wl.dx,
+                      "L": wl.L, "screens": S, "realizations_per_step": Rc, "fields_per_step": B,
+                      "screens_per_step": Rc * S, "field_screen_steps_per_step": B * S,
+                      "note": "SI of the plane wave over the whole grid; subharmonic screens are not periodic, "
+                              "so the periodic grid adds seam scintillation above sigma_R^2 (informational)"},
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
+                        "scope": "whole step (all kernels), algorithmic bytes per step / device time per step",
+                        "algorithmic_bytes_per_step": int(step_bytes)},
+           "si": si}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def run_d2nn(args):
+    """Differentiable path (N = 512, dx = 1 mm, L = 1 km, 10 screens, Cn^2 = 5e-16, Gaussian 2 cm,
+    batch 64, masks seeded N(0, 0.1 rad)): one step = forward propagation of the batch (screens
+    regenerated from the seed), the two-mask receiver and its MAE loss against the apertured vacuum
+    intensity, then the receiver adjoint (mask gradients) and the adjoint propagation (screens
+    regenerated again).  Units: 64 x 10 forward + 64 x 10 adjoint field-screen steps."""
+    import numpy as np
+    import torch
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.config5()
+    N, S, B, AP = wl.N, wl.S, wl.realizations, wl.extra["aperture"]
+    plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
+    plan.set_sources(wl.w0)
+    vac = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, [0.0] * S, max_batch=1)
+    vac.set_sources(wl.w0)
+    th1 = torch.from_numpy(np.random.default_rng(wl.seed).normal(0, 0.1, (N, N)).astype(np.float32)).to(dev)
+    th2 = torch.from_numpy(np.random.default_rng(wl.seed + 1).normal(0, 0.1, (N, N)).astype(np.float32)).to(dev)
+    Uv = torch.zeros((1, N, N), dtype=torch.complex64, device=dev)
+    vac.propagate(Uv, 1, flags=ts.TS_PROP_SOURCE)
+    z = torch.zeros((N, N), dtype=torch.float32, device=dev)
+    Iv = torch.zeros((1, N, N), dtype=torch.float32, device=dev)
+    vac.d2nn_forward(Uv, 1, z, z, AP, z, 1, torch.zeros((3, 1, N, N), dtype=torch.complex64, device=dev), Iv,
+                     torch.zeros(1, dtype=torch.float64, device=dev))
+    Iref = Iv[0].contiguous()
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=dev)
+    ws = torch.zeros((3, B, N, N), dtype=torch.complex64, device=dev)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g1, g2 = torch.zeros_like(z), torch.zeros_like(z)
+    gU = torch.zeros_like(U)
+    real0 = rank * 1000000
+
+    def step(k):
+        real = real0 + k * B
+        plan.propagate(U, B, flags=ts.TS_PROP_SOURCE, seed=wl.seed, real_base=real)
+        plan.d2nn_forward(U, B, th1, th2, AP, Iref, 0, ws, I, loss)
+        plan.d2nn_backward(B, th1, th2, AP, Iref, 0, ws, I, g1, g2, gU)
+        plan.propagate_backward(gU, B, seed=wl.seed, real_base=real)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = args.steps * 2 * B * S * world
+    # forward and adjoint propagation regenerate one screen per field and step (24 B/px each, read
+    # back as an 8-byte phasor by the row pass); the receiver passes move ~10 field-sized arrays each way
+    step_bytes = (2 * propagate_bytes(N, B, S, 1) + 2 * S * screen_bytes(N, B)
+                  + N * N * B * 8 * 20)
+    peak, peak_src = hbm_peak()
+    gbs = step_bytes / (ms / args.steps * 1e-3) / 1e9
+    res = {"metric": "field·screen steps/s, differentiable path (forward + adjoint, two-mask receiver)",
+           "value": round(units / (ms * 1e-3), 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (loss f64)", "data": "synthetic",
+           "config": {"workload": "d2nn N=512 S=10 B=64, MAE loss, screens regenerated from the seed", "N": N,
+                      "dx": wl.dx, "L": wl.L, "screens": S, "batch": B, "aperture_m": AP,
+                      "field_screen_steps_per_step": 2 * B * S},
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
+                        "scope": "whole step (all kernels), algorithmic bytes per step / device time per step",
+                        "algorithmic_bytes_per_step": int(step_bytes)},
+           "last_loss": float(loss.item()), "grad_norms": [float(g1.norm().item()), float(g2.norm().item())]}
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -509,6 +710,10 @@ def main():
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "monte-carlo":
+        run_monte_carlo(args)
+    elif args.workload == "d2nn":
+        run_d2nn(args)
     else:
         run_gpu(args)
 
