@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--no-split-bf16", action="store_true",
                     help="skip the split-BF16 tensor-core comparison (profiling runs)")
-    ap.add_argument("--workload", default="ar-evolution", choices=["ar-evolution", "uneven", "monte-carlo", "d2nn"],
+    ap.add_argument("--workload", default="ar-evolution",
+                    choices=["ar-evolution", "uneven", "monte-carlo", "d2nn", "single-path"],
                     help="ar-evolution: the headline N=1024 workload; uneven: 64-instance persistent batch")
     return ap.parse_args()
 
@@ -704,6 +705,88 @@ def run_d2nn(args):
         print(json.dumps(res), flush=True)
 
 
+def run_single_path(args):
+    """One path (N = 128, dx = 2 mm, L = 1 km, 5 screens, Cn^2 = 1e-15, Gaussian w0 = 2 cm): one step
+    = one ts_propagate call from the source with every screen regenerated from the seed (screen
+    synthesis + column + row pass per step), captured once in a CUDA graph and replayed, so the
+    number is the device latency of a whole path.  Also reported: the same call launched eagerly."""
+    import torch
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.config1()
+    N, S = wl.N, wl.S
+    plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=1)
+    plan.set_sources(wl.w0)
+    U = torch.zeros((1, N, N), dtype=torch.complex64, device=dev)
+    side = torch.cuda.Stream(dev)
+    real = [rank * 1000000]
+
+    def path(stream):
+        plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE, seed=wl.seed, real_base=real[0], stream=stream)
+
+    # eager launches
+    for _ in range(args.warmup):
+        path(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    n_eager = min(args.steps, 256)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n_eager):
+        path(torch.cuda.current_stream(dev))
+    e1.record()
+    torch.cuda.synchronize()
+    eager_us = e0.elapsed_time(e1) * 1e3 / n_eager
+    # the same call captured once in a CUDA graph
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        path(side)  # warm the side stream before capture
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            path(side)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / args.steps
+    # the same path as a one-instance uneven batch: screen synthesis + ONE persistent propagation launch,
+    # replayed as the batch's CUDA graph
+    Ub = torch.zeros((N, N), dtype=torch.complex64, device=dev)
+    batch = ts.Batch([dict(plan=plan, field=Ub, phasor=None, seed=wl.seed, real=real[0], source=True)], timeout_s=5.0)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        batch.run()
+    e1.record()
+    torch.cuda.synchronize()
+    batch_us = e0.elapsed_time(e1) * 1e3 / args.steps
+    batch_ok = batch.status() == 0
+    launches = 3 + 2 * S  # screen synthesis (column + row pass, all 5 screens), first row pass, 5 x (column, row)
+    res = {"metric": "µs per path (device latency, CUDA-graph replay), N=128 single path", "value": round(us, 2),
+           "unit": "us/path", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(us * 1e-3, 5), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "single path N=128 S=5 (config 1), screens regenerated from the seed", "N": N,
+                      "dx": wl.dx, "L": wl.L, "screens": S, "launches_per_path": launches},
+           "eager_us_per_path": round(eager_us, 2),
+           "batch_us_per_path": round(batch_us, 2) if batch_ok else None,
+           "field_screen_steps_per_s": round(S * world / (us * 1e-6), 1)}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -714,6 +797,8 @@ def main():
         run_monte_carlo(args)
     elif args.workload == "d2nn":
         run_d2nn(args)
+    elif args.workload == "single-path":
+        run_single_path(args)
     else:
         run_gpu(args)
 

@@ -99,15 +99,16 @@ void free_plan(Plan* p)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// regenerate screen `s` of the G screen sets (realizations real_base .. real_base + G - 1) into ws_phi
+// regenerate screen `s` of the G screen sets (realizations real_base .. real_base + G - 1) into ws_phi,
+// or (s < 0, regen_all plans) all S screens of the G sets at once, ws_phi laid out [G][S][N][N]
 ts_status regen_screen(Plan& p, uint64_t seed, uint32_t real_base, int G, int s, cudaStream_t st)
 {
     ScreenArgs a{};
     a.seed = seed;
-    a.s_begin = s;
-    a.s_count = 1;
+    a.s_begin = s < 0 ? 0 : s;
+    a.s_count = s < 0 ? p.S : 1;
     a.r_begin = real_base;
-    a.items = G;
+    a.items = G * a.s_count;
     a.t = 0;
     a.phi = nullptr;
     a.phasor = p.ws_phi;
@@ -154,10 +155,18 @@ ts_status prop_range(Plan& p, float2* U, int b0, int B, const float* phi, const 
             ra.phi = phi + set0 + (size_t)s * N2;
             rf |= RP_PHASE;
         } else {
-            // regenerated screens: one per screen set of this range, realizations real_base + set index
-            if ((stt = regen_screen(p, seed, real_base + (uint32_t)(b0 / phi_group), G, s, st)) != TS_OK) return stt;
-            ra.phasor = p.ws_phi;
-            ra.phi_set_stride = (long long)N2;
+            // regenerated screens: one per screen set of this range, realizations real_base + set index;
+            // all S of them in one synthesis launch when the workspace holds them, else step by step
+            const uint32_t rb = real_base + (uint32_t)(b0 / phi_group);
+            if (p.regen_all) {
+                if (s == 0 && (stt = regen_screen(p, seed, rb, G, -1, st)) != TS_OK) return stt;
+                ra.phasor = p.ws_phi + (size_t)s * N2;
+                ra.phi_set_stride = (long long)S * N2;
+            } else {
+                if ((stt = regen_screen(p, seed, rb, G, s, st)) != TS_OK) return stt;
+                ra.phasor = p.ws_phi;
+                ra.phi_set_stride = (long long)N2;
+            }
             ra.b0 = b0 % phi_group;  // sets counted from this range's first set
             rf |= RP_PHASOR;
         }
@@ -484,7 +493,9 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         ok(dalloc(*p, &p->ws_sha, (size_t)p->screen_chunk * kShCoef));
     }
     ok(dalloc(*p, &p->ws_y, (size_t)p->screen_chunk * N2));
-    ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * N2));  // regenerated screens as exp(i phi)
+    // regenerated screens as exp(i phi): all S steps of a call at once when that takes <= 256 MiB
+    p->regen_all = (size_t)max_batch * S * N2 * sizeof(float2) <= (256ull << 20);
+    ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * (p->regen_all ? S : 1) * N2));
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
     if (p->split_bf16) {
         ok(dalloc(*p, &p->d_err, 1));
@@ -746,9 +757,14 @@ ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* ph
             phase_flag = RP_PHASE;
             return TS_OK;
         }
+        phase_flag = RP_PHASOR;
+        if (p->regen_all) {  // all S screens synthesised with the first (last-step) screen
+            ra.phasor = p->ws_phi + (size_t)s * N2;
+            ra.phi_set_stride = (long long)S * N2;
+            return s == S - 1 ? regen_screen(*p, seed, real_base, G, -1, st) : TS_OK;
+        }
         ra.phasor = p->ws_phi;
         ra.phi_set_stride = (long long)N2;
-        phase_flag = RP_PHASOR;
         return regen_screen(*p, seed, real_base, G, s, st);
     };
     if ((stt = set_screen(S - 1)) != TS_OK) return stt;

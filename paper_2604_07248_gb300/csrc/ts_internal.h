@@ -58,7 +58,9 @@ struct Plan {
     float* ws_shv = nullptr;      // [screen_chunk][7][N] subharmonic row vectors
     float* ws_shmean = nullptr;   // [screen_chunk] subharmonic piston
     double2* ws_sha = nullptr;    // [screen_chunk][27] subharmonic coefficients
-    float2* ws_phi = nullptr;     // [max_batch][N][N] regenerated screens as exp(i phi) (phi == NULL paths)
+    float2* ws_phi = nullptr;     // regenerated screens as exp(i phi) (phi == NULL paths): [max_batch][S][N][N]
+                                  // when regen_all, else [max_batch][N][N] (one step at a time)
+    bool regen_all = false;       // all S screens of a call synthesised in one launch (small workspaces)
     double* ws_rows = nullptr;    // [max_batch][N][2] per-row beam sums
     size_t bytes = 0;
 

@@ -58,7 +58,18 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
     const float amp = __ldg(a.amp + s);
     stage_twiddles<N>(tw, a.tw);
 
+    // The PSD shape and (AR step) the previous state are loaded first, so their latency overlaps the
+    // Philox / Box-Muller arithmetic that follows; the arithmetic itself is unchanged.
     float2 v[E];
+    float gv[E];
+    float2* sp = a.spec + (size_t)z * N * N + n;
+#pragma unroll
+    for (int i = 0; i < E; ++i) gv[i] = __ldg(a.g + (size_t)(t + i * T) * N + n);
+    if constexpr (MODE == SC_AR_STEP) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = sp[(size_t)(t + i * T) * N];
+    }
+    const float2 tx = (MODE == SC_AR_STEP && a.tilt) ? __ldg(a.tilt + n) : make_float2(1.0f, 0.0f);
     // bins (m, n) and (m + N/2, n) share one Philox call: registers i and i + E/2
 #pragma unroll
     for (int i = 0; i < E / 2; ++i) {
@@ -66,20 +77,19 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
         const u32x4 w = philox4x32_10(u32x4{(uint32_t)(m * N + n), (uint32_t)s, r, a.tag}, a.k0, a.k1);
         const float2 c0 = box_muller(w.a, w.b);
         const float2 c1 = box_muller(w.c, w.d);
-        const float s0 = amp * __ldg(a.g + (size_t)m * N + n);
-        const float s1 = amp * __ldg(a.g + (size_t)(m + N / 2) * N + n);
-        v[i] = cscale(c0, s0);
-        v[i + E / 2] = cscale(c1, s1);
-    }
-    float2* sp = a.spec + (size_t)z * N * N + n;
-    if constexpr (MODE == SC_AR_STEP) {
-        const float2 tx = a.tilt ? __ldg(a.tilt + n) : make_float2(1.0f, 0.0f);
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + i * T;
-            float2 old = sp[(size_t)m * N];
-            if (a.tilt) old = cmul(old, cmul(tx, __ldg(a.tilt + N + m)));
-            v[i] = make_float2(fmaf(a.alpha, old.x, a.beta * v[i].x), fmaf(a.alpha, old.y, a.beta * v[i].y));
+        const float2 n0 = cscale(c0, amp * gv[i]);
+        const float2 n1 = cscale(c1, amp * gv[i + E / 2]);
+        if constexpr (MODE == SC_AR_STEP) {
+            float2 o0 = v[i], o1 = v[i + E / 2];
+            if (a.tilt) {
+                o0 = cmul(o0, cmul(tx, __ldg(a.tilt + N + m)));
+                o1 = cmul(o1, cmul(tx, __ldg(a.tilt + N + m + N / 2)));
+            }
+            v[i] = make_float2(fmaf(a.alpha, o0.x, a.beta * n0.x), fmaf(a.alpha, o0.y, a.beta * n0.y));
+            v[i + E / 2] = make_float2(fmaf(a.alpha, o1.x, a.beta * n1.x), fmaf(a.alpha, o1.y, a.beta * n1.y));
+        } else {
+            v[i] = n0;
+            v[i + E / 2] = n1;
         }
     }
     if constexpr (MODE != SC_INDEP) {

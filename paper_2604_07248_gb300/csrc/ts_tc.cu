@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(kTcRows) tc_dft32_kernel(const float2* __restr
         tc::mbar_init(mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the whole operand window starts zeroed, so a descriptor that reads outside the staged data (the
+    // exchanged-stride check, layout 2) sees zeros rather than stale shared memory
+    for (int i = tid; i < kWindow / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
     // G' = [G_hi ; G_lo ; G_hi] stored K-major (row n, column k)
     for (int idx = tid; idx < kTcN * (kTcK / 2); idx += blockDim.x) {
         const int n = idx / (kTcK / 2), k = 2 * (idx % (kTcK / 2));

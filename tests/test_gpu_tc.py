@@ -43,4 +43,6 @@ def test_tc_mn_major_descriptor_reading():
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     ref = np.fft.fft(x.astype(np.complex128), axis=1)
-    assert np.linalg.norm(Xd.cpu().numpy() - ref) / np.linalg.norm(ref) > 0.1
+    got = Xd.cpu().numpy()
+    assert np.all(np.isfinite(got))  # the operand window is zeroed before staging
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) > 0.1
