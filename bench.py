@@ -378,7 +378,8 @@ def run_gpu(args):
                    "cn2": wl.cn2[0], "alpha": wl.alpha, "field_screen_steps_per_step": B * S,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "autotune": dict(zip(("points_per_thread", "us_e16", "us_e32", "streams", "us_streams_1_2_4",
-                                         "col_variant", "us_e32_warp_columns"),
+                                         "col_variant", "us_e32_warp_columns", "row_variant",
+                                         "us_e32_shared_phasor_rows"),
                                         [round(x, 2) if isinstance(x, float) else
                                          ([round(y, 2) for y in x] if isinstance(x, list) else x)
                                          for x in plan.tuning()])),

@@ -112,15 +112,18 @@ size_t ts_plan_device_bytes(ts_plan plan);
  *  - the propagation passes run with `points_per_thread` FFT points per thread (16 or 32) and, for
  *    N = 1024 with 32 points, `col_variant` 0 (a column line spread over four warps, block-level
  *    exchanges) or 1 (one warp per column, the CTA's 8-column tile staged through shared memory);
- *    us_e16 / us_e32 / us_e32_warp_columns receive the timed cost in microseconds of one column + one
- *    row pass of each candidate;
+ *    `row_variant` 0 (each CTA reads its rows of the screen phasor) or 1 (N = 1024, 32 points, phasor
+ *    screens shared by 2, 4 or 8 fields: a CTA holds those fields' rows and stages the phasor rows
+ *    once in shared memory); us_e16 / us_e32 / us_e32_warp_columns / us_e32_shared_phasor_rows
+ *    receive the timed cost in microseconds of one column + one row pass of each candidate;
  *  - `streams` = number of field groups ts_propagate runs concurrently on the plan's own streams when
  *    the screens are given (1, 2 or 4; forked from and joined back to the caller's stream);
  *    us_streams[3] receives the timed cost for 1, 2 and 4 groups.
  * Outputs other than points_per_thread may be NULL; a 0 timing means not timed (N <= 256, a cached
- * result, or TS_FFT_E / TS_COL_VARIANT / TS_PROP_STREAMS set in the environment). */
+ * result, or TS_FFT_E / TS_COL_VARIANT / TS_ROW_VARIANT / TS_PROP_STREAMS set in the environment). */
 ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
-                         float* us_streams, int* col_variant, float* us_e32_warp_columns);
+                         float* us_streams, int* col_variant, float* us_e32_warp_columns, int* row_variant,
+                         float* us_e32_shared_phasor_rows);
 
 /* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
  * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */

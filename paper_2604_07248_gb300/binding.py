@@ -61,7 +61,8 @@ SIGNATURES = {
     "ts_plan_device_status": (_I, [_P]),
     "ts_plan_device_bytes": (C.c_size_t, [_P]),
     "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float),
-                            C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+                            C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float),
+                            C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_plan_set_sources": (_I, [_P, _I, _P]),
     "ts_make_sources": (_I, [_P, _P, _I, _P]),
@@ -200,12 +201,14 @@ class Plan:
 
     def tuning(self):
         """(points per thread, us for E=16, us for E=32, concurrent field groups, us for 1/2/4 groups,
-        column variant, us for E=32 with warp-owned columns)."""
+        column variant, us for E=32 with warp-owned columns, row variant, us for E=32 with shared
+        phasor rows)."""
         e, a, b, g, v, w = C.c_int(), C.c_float(), C.c_float(), C.c_int(), C.c_int(), C.c_float()
+        rv, rw = C.c_int(), C.c_float()
         us = (C.c_float * 3)()
         _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b), C.byref(g), us, C.byref(v),
-                                     C.byref(w)), "ts_plan_tuning")
-        return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]], v.value, w.value
+                                     C.byref(w), C.byref(rv), C.byref(rw)), "ts_plan_tuning")
+        return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]], v.value, w.value, rv.value, rw.value
 
     def device_status(self):
         """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a tensor-core wait of a

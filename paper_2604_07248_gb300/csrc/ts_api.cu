@@ -196,6 +196,7 @@ std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 ts_status autotune(Plan& p)
 {
     p.col_variant = 0;
+    p.row_variant = 0;
     if (p.split_bf16) {
         p.fft_e = 32;  // the tensor-core passes have one configuration
         return TS_OK;
@@ -204,16 +205,19 @@ ts_status autotune(Plan& p)
         p.fft_e = 16;
         return TS_OK;
     }
-    // candidates (points per thread, column variant), filtered by TS_FFT_E / TS_COL_VARIANT
-    int force_e = 0, force_v = -1;
+    // candidates (points per thread, column variant, row variant), filtered by TS_FFT_E / TS_COL_VARIANT /
+    // TS_ROW_VARIANT; the variants other than 0 exist for N = 1024 at 32 points per thread
+    int force_e = 0, force_v = -1, force_r = -1;
     if (const char* env = std::getenv("TS_FFT_E")) force_e = std::atoi(env);
     if (const char* env = std::getenv("TS_COL_VARIANT")) force_v = std::atoi(env);
-    const int cand_e[3] = {16, 32, 32}, cand_v[3] = {0, 0, 1};
-    bool use[3];
+    if (const char* env = std::getenv("TS_ROW_VARIANT")) force_r = std::atoi(env);
+    constexpr int kCand = 4;
+    const int cand_e[kCand] = {16, 32, 32, 32}, cand_v[kCand] = {0, 0, 1, 0}, cand_r[kCand] = {0, 0, 0, 1};
+    bool use[kCand];
     int n_use = 0, only = -1;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < kCand; ++c) {
         use[c] = (force_e == 0 || force_e == cand_e[c]) && (force_v < 0 || force_v == cand_v[c]) &&
-                 (cand_v[c] == 0 || p.N == 1024);
+                 (force_r < 0 || force_r == cand_r[c]) && ((cand_v[c] == 0 && cand_r[c] == 0) || p.N == 1024);
         if (use[c]) {
             ++n_use;
             only = c;
@@ -226,17 +230,20 @@ ts_status autotune(Plan& p)
     if (n_use == 1) {
         p.fft_e = cand_e[only];
         p.col_variant = cand_v[only];
+        p.row_variant = cand_r[only];
         return TS_OK;
     }
     const size_t N2 = (size_t)p.N * p.N;
     const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
-    const auto key = std::make_tuple(p.device, p.N, Bt, (p.sep_transfer ? 1 : 0) + 2 * (force_e + 64 * (force_v + 1)));
+    const auto key =
+        std::make_tuple(p.device, p.N, Bt, (p.sep_transfer ? 1 : 0) + 2 * (force_e + 64 * (force_v + 1) + 256 * (force_r + 1)));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             p.fft_e = cand_e[it->second];
             p.col_variant = cand_v[it->second];
+            p.row_variant = cand_r[it->second];
             return TS_OK;
         }
     }
@@ -247,10 +254,11 @@ ts_status autotune(Plan& p)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 1e30f;
     int best_c = 1;
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    for (int c = 0; c < kCand && e == cudaSuccess; ++c) {
         if (!use[c]) continue;
         p.fft_e = cand_e[c];
         p.col_variant = cand_v[c];
+        p.row_variant = cand_r[c];
         RowArgs ra{};
         ra.field = p.ws_y;
         ra.phasor = p.ws_phi;
@@ -281,6 +289,7 @@ ts_status autotune(Plan& p)
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune");
     p.fft_e = cand_e[best_c];
     p.col_variant = cand_v[best_c];
+    p.row_variant = cand_r[best_c];
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best_c;
     return TS_OK;
@@ -304,7 +313,7 @@ ts_status autotune_groups(Plan& p)
         }
     }
     const auto key = std::make_tuple(p.device, p.N, Bt, p.sep_transfer ? 1 : 0,
-                                     p.split_bf16 ? -1 : p.fft_e + 1000 * p.col_variant);
+                                     p.split_bf16 ? -1 : p.fft_e + 1000 * p.col_variant + 2000 * p.row_variant);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_group_cache.find(key);
@@ -574,7 +583,8 @@ ts_status ts_plan_destroy(ts_plan plan)
 size_t ts_plan_device_bytes(ts_plan plan) { return plan ? reinterpret_cast<Plan*>(plan)->bytes : 0; }
 
 ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
-                         float* us_streams, int* col_variant, float* us_e32_warp_columns)
+                         float* us_streams, int* col_variant, float* us_e32_warp_columns, int* row_variant,
+                         float* us_e32_shared_phasor_rows)
 {
     if (!plan || !points_per_thread) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning: need plan and output");
     Plan* p = reinterpret_cast<Plan*>(plan);
@@ -586,6 +596,8 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
         for (int i = 0; i < 3; ++i) us_streams[i] = p->tune_group_us[i];
     if (col_variant) *col_variant = p->col_variant;
     if (us_e32_warp_columns) *us_e32_warp_columns = p->tune_us[2];
+    if (row_variant) *row_variant = p->row_variant;
+    if (us_e32_shared_phasor_rows) *us_e32_shared_phasor_rows = p->tune_us[3];
     return TS_OK;
 }
 

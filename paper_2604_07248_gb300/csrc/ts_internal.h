@@ -37,7 +37,9 @@ struct Plan {
     long long tc_budget = 0;   // clock64 cycles a tensor-core wait may take
     int tc_col_groups = 1;     // tensor-core column tiles: 1 = 4 columns (4 CTAs / SM), 2 = 8 columns (2 CTAs / SM)
     int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column (N = 1024, E = 32)
-    float tune_us[3] = {0, 0, 0};  // autotuner timings of one column + row pass: E = 16, E = 32, E = 32 warp columns
+    int row_variant = 0;       // row pass: 0 = per-CTA screen rows, 1 = phasor rows shared by the CTA's fields
+    float tune_us[4] = {0, 0, 0, 0};  // autotuner timings of one column + row pass per candidate (E, col, row):
+                                      // (16,0,0), (32,0,0), (32,1,0), (32,0,1)
     int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups

@@ -50,11 +50,11 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
     rp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
     if (p.split_bf16) return tc_row_pass(flags, rp, a.B, p.tc_budget, p.d_err, st);
     switch (p.N) {
-    case 128: return row_pass_n<128>(p.fft_e, flags, rp, a.B, st);
-    case 256: return row_pass_n<256>(p.fft_e, flags, rp, a.B, st);
-    case 512: return row_pass_n<512>(p.fft_e, flags, rp, a.B, st);
-    case 1024: return row_pass_n<1024>(p.fft_e, flags, rp, a.B, st);
-    case 2048: return row_pass_n<2048>(p.fft_e, flags, rp, a.B, st);
+    case 128: return row_pass_n<128>(p.fft_e, p.row_variant, flags, rp, a.B, st);
+    case 256: return row_pass_n<256>(p.fft_e, p.row_variant, flags, rp, a.B, st);
+    case 512: return row_pass_n<512>(p.fft_e, p.row_variant, flags, rp, a.B, st);
+    case 1024: return row_pass_n<1024>(p.fft_e, p.row_variant, flags, rp, a.B, st);
+    case 2048: return row_pass_n<2048>(p.fft_e, p.row_variant, flags, rp, a.B, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -33,8 +33,10 @@ struct ColParams {
 };
 
 // Per-N entry points, instantiated in ts_prop_n<N>.cu (one translation unit per N builds in parallel).
+// variant 0: each CTA reads its own screen rows; variant 1 (N = 1024, E = 32, phasor screens): the
+// CTA's fields share one screen set and its phasor rows are staged once in shared memory
 template <int N>
-cudaError_t row_pass_n(int E, int flags, const RowParams& rp, int B, cudaStream_t st);
+cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B, cudaStream_t st);
 // variant 0: column lines shared by several warps (block synchronisation); variant 1 (N = 1024,
 // E = 32): one warp per column, tile staged through shared memory
 template <int N>

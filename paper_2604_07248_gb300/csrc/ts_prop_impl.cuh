@@ -126,6 +126,85 @@ __global__ void __launch_bounds__(kRowThreads, (FftCfg<N, EE>::E >= 32 ? 2 : 4))
 
 
 
+// Row pass with the screen phasor shared through shared memory (E = 32, one warp per row): the CTA's
+// 8 warps are 8 / FPC rows x FPC fields that use the same screen set, so each phasor row is read from
+// memory once per CTA, at kernel start (its latency overlaps the field loads and the inverse FFT),
+// instead of once per field after the inverse FFT.  Requires the FPC fields of a CTA to share one set.
+template <int N>
+struct RowShCfg {
+    using C = FftCfg<N, 32>;
+    static_assert(C::T == 32, "one warp per row");
+    static constexpr int LS = C::padded;
+    static constexpr size_t smem(int fpc) { return sizeof(float2) * (C::tw_smem + (8 / fpc) * N + 8 * LS); }
+};
+
+template <int N, int FLAGS, int FPC>
+__global__ void __launch_bounds__(kRowThreads, 2) row_pass_shared_kernel(const RowParams a)
+{
+    static_assert(FLAGS & RP_PHASOR, "shared phasor rows");
+    using C = typename RowShCfg<N>::C;
+    constexpr int E = C::E, T = C::T, RPC = 8 / FPC;
+    extern __shared__ float2 smem[];
+    float2* tw = smem;
+    float2* phs = smem + C::tw_smem;
+    const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const int rsub = warp / FPC, f = warp % FPC;
+    const int j0 = blockIdx.x * RPC, j = j0 + rsub;
+    const int b = blockIdx.y * FPC + f;
+    float2* buf = phs + RPC * N + warp * RowShCfg<N>::LS;
+    float2* row = a.field + ((size_t)b * N + j) * N;
+    // the field row first (its loads are in flight while the twiddles and phasor rows are staged)
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = row[t + i * T];
+    stage_twiddles_c<C>(tw, a.tw);
+    {
+        const int set = (blockIdx.y * FPC + a.phi_off) / a.phi_group;
+        const float4* src = reinterpret_cast<const float4*>(a.phasor + (long long)set * a.phi_set_stride + (size_t)j0 * N);
+        float4* dst = reinterpret_cast<float4*>(phs);
+        for (int i = threadIdx.x; i < RPC * N / 2; i += kRowThreads) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    if constexpr (FLAGS & RP_IN_FREQ) line_fft_c<C, +1>(v, buf, t, tw, WarpBar());
+    const float2* ph = phs + rsub * N;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const float2 e = ph[t + i * T];
+        v[i] = a.phase_sign > 0.0f ? cmul(v[i], e) : cmulc(v[i], e);
+    }
+    if constexpr (FLAGS & RP_INTENSITY) {
+        float s0 = 0.0f, s1 = 0.0f;
+        const float y = (float)(j - N / 2);
+        float* irow = a.intensity + ((size_t)b * N + j) * N;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float I = v[i].x * v[i].x + v[i].y * v[i].y;
+            const float x = (float)(t + i * T - N / 2);
+            irow[t + i * T] = I;
+            s0 += I;
+            s1 = fmaf(x * x + y * y, I, s1);
+        }
+        if (a.rows != nullptr) {
+            double d0 = s0, d1 = s1;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                d0 += __shfl_down_sync(0xffffffffu, d0, off);
+                d1 += __shfl_down_sync(0xffffffffu, d1, off);
+            }
+            if (t == 0) {
+                double* dst = a.rows + ((size_t)b * N + j) * 2;
+                dst[0] = d0;
+                dst[1] = d1;
+            }
+        }
+    }
+    if constexpr (FLAGS & RP_OUT_FREQ) line_fft_c<C, -1>(v, buf, t, tw, WarpBar());
+    if constexpr (FLAGS & RP_STORE) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) row[t + i * T] = v[i];
+    }
+}
+
 template <int N, int E>
 struct ColCfg {
     using C = FftCfg<N, E>;
@@ -323,6 +402,32 @@ cudaError_t row_dispatch(int flags, const RowParams& rp, int B, cudaStream_t st)
     }
 }
 
+template <int N, int FLAGS, int FPC>
+cudaError_t row_launch_shared(const RowParams& rp, int B, cudaStream_t st)
+{
+    dim3 grid(N / (8 / FPC), B / FPC);
+    row_pass_shared_kernel<N, FLAGS, FPC><<<grid, kRowThreads, RowShCfg<N>::smem(FPC), st>>>(rp);
+    return cudaGetLastError();
+}
+
+// the shared-phasor row pass for the flag sets that modulate by a phasor; returns
+// cudaErrorNotSupported when the combination has no shared variant
+template <int N, int FPC>
+cudaError_t row_dispatch_shared(int flags, const RowParams& rp, int B, cudaStream_t st)
+{
+    switch (flags) {
+    case RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE:
+        return row_launch_shared<N, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, FPC>(rp, B, st);
+    case RP_IN_FREQ | RP_PHASOR | RP_STORE: return row_launch_shared<N, RP_IN_FREQ | RP_PHASOR | RP_STORE, FPC>(rp, B, st);
+    case RP_IN_FREQ | RP_PHASOR | RP_INTENSITY | RP_STORE:
+        return row_launch_shared<N, RP_IN_FREQ | RP_PHASOR | RP_INTENSITY | RP_STORE, FPC>(rp, B, st);
+    case RP_IN_FREQ | RP_PHASOR | RP_INTENSITY:
+        return row_launch_shared<N, RP_IN_FREQ | RP_PHASOR | RP_INTENSITY, FPC>(rp, B, st);
+    case RP_PHASOR | RP_OUT_FREQ | RP_STORE: return row_launch_shared<N, RP_PHASOR | RP_OUT_FREQ | RP_STORE, FPC>(rp, B, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 template <int N, int E, bool CONJ, bool SEP>
 cudaError_t col_launch(const ColParams& cp, int B, cudaStream_t st)
 {
@@ -354,6 +459,22 @@ template <int N, int E, int FLAGS>
 cudaError_t row_attr()
 {
     return smem_attr(row_pass_kernel<N, E, FLAGS>, (int)RowCfg<N, E>::smem);
+}
+
+template <int N, int FPC>
+cudaError_t row_attr_shared()
+{
+    cudaError_t e = cudaSuccess;
+    const int sz = (int)RowShCfg<N>::smem(FPC);
+    auto chk = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    chk(smem_attr(row_pass_shared_kernel<N, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, FPC>, sz));
+    chk(smem_attr(row_pass_shared_kernel<N, RP_IN_FREQ | RP_PHASOR | RP_STORE, FPC>, sz));
+    chk(smem_attr(row_pass_shared_kernel<N, RP_IN_FREQ | RP_PHASOR | RP_INTENSITY | RP_STORE, FPC>, sz));
+    chk(smem_attr(row_pass_shared_kernel<N, RP_IN_FREQ | RP_PHASOR | RP_INTENSITY, FPC>, sz));
+    chk(smem_attr(row_pass_shared_kernel<N, RP_PHASOR | RP_OUT_FREQ | RP_STORE, FPC>, sz));
+    return e;
 }
 
 template <int N, int E>
@@ -390,8 +511,23 @@ cudaError_t prepare_prop_for()
 }  // namespace
 
 template <int N>
-cudaError_t row_pass_n(int E, int flags, const RowParams& rp, int B, cudaStream_t st)
+cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B, cudaStream_t st)
 {
+    if constexpr (N == 1024) {
+        // shared phasor rows: FPC consecutive fields of one screen set per CTA
+        // (the phasor rows are staged with 16-byte loads: only for 16-byte aligned phasor arrays)
+        if (variant == 1 && E == 32 && (flags & RP_PHASOR) && (reinterpret_cast<uintptr_t>(rp.phasor) & 15) == 0 &&
+            (rp.phi_set_stride & 1) == 0) {
+            for (int fpc = 8; fpc >= 2; fpc >>= 1) {
+                if (B % fpc || rp.phi_group % fpc || rp.phi_off % fpc) continue;
+                cudaError_t e = fpc == 8 ? row_dispatch_shared<N, 8>(flags, rp, B, st)
+                                : fpc == 4 ? row_dispatch_shared<N, 4>(flags, rp, B, st)
+                                           : row_dispatch_shared<N, 2>(flags, rp, B, st);
+                if (e != cudaErrorNotSupported) return e;
+                break;
+            }
+        }
+    }
     if constexpr (N <= 256) {
         return row_dispatch<N, 16>(flags, rp, B, st);
     } else {
@@ -431,6 +567,9 @@ cudaError_t prepare_prop_n()
         cudaError_t e = prepare_prop_for<N, 16>();
         if (e == cudaSuccess) e = prepare_prop_for<N, 32>();
         if constexpr (N == 1024) {
+            if (e == cudaSuccess) e = row_attr_shared<N, 8>();
+            if (e == cudaSuccess) e = row_attr_shared<N, 4>();
+            if (e == cudaSuccess) e = row_attr_shared<N, 2>();
             const int ws = (int)ColWarpCfg<N>::smem;
             if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, false, false>, ws);
             if (e == cudaSuccess) e = smem_attr(col_pass_warp_kernel<N, true, false>, ws);

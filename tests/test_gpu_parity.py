@@ -357,9 +357,10 @@ def test_both_fft_variants_match_oracle(E, variant, monkeypatch):
     # must agree with the oracle, forward and adjoint
     monkeypatch.setenv("TS_FFT_E", str(E))
     monkeypatch.setenv("TS_COL_VARIANT", str(variant))
+    monkeypatch.setenv("TS_ROW_VARIANT", "0")
     N, dx, S = 1024, 5e-4, 3
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
-    assert plan.tuning()[0] == E and plan.tuning()[5] == variant
+    assert plan.tuning()[0] == E and plan.tuning()[5] == variant and plan.tuning()[7] == 0
     plan.set_sources([0.01, 0.02])
     U = cfield(2, N)
     plan.propagate(U, 2, flags=ts.TS_PROP_SOURCE, seed=4)
@@ -373,6 +374,42 @@ def test_both_fft_variants_match_oracle(E, variant, monkeypatch):
         assert rel_l2(U[b].cpu().numpy(), ref) < TOL
         back = O.propagate_adjoint(md, [62.5] * S, phis[b], U[b].cpu().numpy())
         assert rel_l2(g[b].cpu().numpy(), back) < TOL
+
+
+@pytest.mark.parametrize("B,phi_group", [(4, 2), (8, 8), (3, 3)])
+def test_shared_phasor_row_pass_matches_oracle(B, phi_group, monkeypatch):
+    # row variant 1 (N = 1024, 32 points per thread): the fields of a CTA share one screen set and its
+    # phasor rows are staged once in shared memory; 2, 8 and (no divisor of 3: the per-CTA-rows
+    # fallback) fields per set; forward with intensity and beam sums, then the adjoint
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "0")
+    monkeypatch.setenv("TS_ROW_VARIANT", "1")
+    monkeypatch.setenv("TS_PROP_STREAMS", "1")
+    N, dx, S = 1024, 5e-4, 3
+    G = (B + phi_group - 1) // phi_group
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    assert plan.tuning()[7] == 1
+    phis = np.stack([np.stack([O.make_screen(md, 1e-14, 62.5, 0, 40, s, g) for s in range(S)]) for g in range(G)])
+    ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
+    rng = np.random.default_rng(41)
+    U0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    U = torch.from_numpy(U0).to(DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    sums = torch.zeros((B, 2), dtype=torch.float64, device=DEV)
+    plan.propagate(U, B, phasor=ph, phi_group=phi_group, flags=ts.TS_PROP_INTENSITY, intensity=I, beam_sums=sums)
+    g = torch.from_numpy(U0).to(DEV)
+    plan.propagate_backward(g, B, phasor=ph, phi_group=phi_group)
+    torch.cuda.synchronize()
+    got, Ig, gg = U.cpu().numpy(), I.cpu().numpy(), g.cpu().numpy()
+    for b in range(B):
+        set_phi = np.angle(np.exp(1j * phis[b // phi_group]))  # the phases the uploaded phasors carry
+        ref = O.propagate(md, [62.5] * S, set_phi, U0[b])
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+        assert rel_l2(Ig[b], np.abs(ref) ** 2) < 2 * TOL
+        assert abs(sums[b, 0].item() / np.sum(np.abs(ref) ** 2) - 1) < 2 * TOL
+        back = O.propagate_adjoint(md, [62.5] * S, set_phi, U0[b])
+        assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
 @pytest.mark.parametrize("groups", [2, 4])
