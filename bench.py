@@ -161,19 +161,21 @@ def screen_bytes(N, n_screens, ar=False):
 
 
 def load_traffic(kind_name):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or None when any source file
-    the kernel is built from changed since the counters were taken."""
+    """(cold-cache DRAM bytes per launch, median warm-cache bytes per 4-field launch) of a kernel from
+    the committed ncu summary, or (None, None) when any source file the kernel is built from changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
-        return None
+        return None, None
     try:
         k = json.load(open(path)).get("kernels", {}).get(kind_name)
     except (OSError, ValueError):
-        return None
+        return None, None
     from paper_2604_07248_gb300 import _build
     if k is None or k.get("sources_sha") != _build.files_sha(k.get("sources", [])):
-        return None
-    return k.get("dram_bytes_per_launch")
+        return None, None
+    warm = k.get("warm_dram_bytes_per_launch_4_fields")
+    return k.get("dram_bytes_per_launch"), (int(statistics.median(warm)) if warm else None)
 
 
 def run_gpu(args):
@@ -281,8 +283,13 @@ def run_gpu(args):
             per_kernel[name]["share"] = round(kt[k][1] / total, 4) if total > 0 else None
     dom = max(per_kernel, key=lambda n: per_kernel[n]["share"] or 0)
     dk = per_kernel[dom]
+    traffic, traffic_warm = load_traffic(dom)
     roof = {"bound": "hbm", "kernel": dom, "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
-            "frac": round(dk["achieved_gbs"] / peak, 4), "traffic": load_traffic(dom), "peak_source": peak_src,
+            "frac": round(dk["achieved_gbs"] / peak, 4), "traffic": traffic,
+            "traffic_note": "ncu dram read + write per 8-field launch, cold caches (ncu flushes before replay); "
+                            "mid-pipeline with warm caches a 4-field launch moves traffic_warm_4_fields bytes: the "
+                            "fields stay L2-resident between the passes",
+            "traffic_warm_4_fields": traffic_warm, "peak_source": peak_src,
             "timing": "per-launch CUDA events on the launching stream, each kernel alone (one stream)",
             "kernels": per_kernel}
 
