@@ -265,6 +265,40 @@ ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* tot
 ts_status ts_tc_dft32(const void* x, void* X, int nvec, int sign, int layout, double timeout_s, int* err,
                       void* stream);
 
+/* ---- path planning (host functions, no GPU) ---------------------------------------------------- */
+
+/* Hufnagel-Valley Cn^2 profile (S21) at n heights h [m] >= 0:
+ *   cn2[i] = 0.00594 (V/27)^2 (1e-5 h)^10 exp(-h/1000) + 2.7e-16 exp(-h/1500) + A exp(-h/100),
+ * V = wind speed [m/s], A = ground-level constant [m^-2/3] (HV5/7: V = 21, A = 1.7e-14).
+ * h, cn2: host arrays of n doubles. */
+ts_status ts_cn2_hufnagel_valley(const double* h, int n, double V, double A, double* cn2);
+
+/* Rytov variance of the interval [z0, z1] of a sampled Cn^2 profile (S19):
+ *   sigma^2 = 3.27 k^(7/6) dz^(5/6) int_0^dz Cn2(z0 + z) (1 - z/dz)^(5/3) dz,  k = 2 pi / lambda.
+ * The profile (host arrays prof_z strictly increasing, prof_cn2 >= 0, n_prof >= 1) is linear
+ * between samples and constant beyond the ends; the integral is evaluated in closed form on each
+ * linear piece.  For a constant profile sigma^2 = 1.226 k^(7/6) Cn2 dz^(11/6). */
+ts_status ts_rytov_interval(const double* prof_z, const double* prof_cn2, int n_prof, double lambda, double z0,
+                            double z1, double* sigma2);
+
+/* Screen placement (Sec. 2.4) over a path [0, L] of a sampled Cn^2 profile (as in ts_rytov_interval):
+ *   1. start from the caller's interval boundaries init_bounds[0..n_init) (values inside (0, L);
+ *      n_init = 0: one interval);
+ *   2. split every interval whose Rytov variance (S19) exceeds rytov_limit at its midpoint until none
+ *      does; 3. merge neighbours while the merged interval stays within the limit;
+ *   4. final placement: a sweep from z = 0 extends each interval until its variance reaches the
+ *      limit (lengths solved by linear interpolation of log sigma^2 against log dz); the sweep is kept
+ *      when it needs no more intervals than steps 2-3;
+ *   5. every interval longer than the Eq. 7 step limit of `grid` is split into equal parts.
+ * Outputs (host arrays of max_screens doubles): dz_out[i] = interval length, cn2_out[i] = the
+ * interval's path-integrated Cn^2 divided by its length (the strength its screen carries, S18),
+ * rytov_out[i] = its Rytov variance (may be NULL); *n_out = number of intervals.  They can be
+ * passed to ts_plan_create as a ts_path.  Errors: TS_ERR_INVALID_ARG, TS_ERR_WORKSPACE (more than
+ * max_screens intervals needed; *n_out still holds the count). */
+ts_status ts_place_screens(const double* prof_z, const double* prof_cn2, int n_prof, const ts_medium* medium,
+                           const ts_grid* grid, double L, const double* init_bounds, int n_init, double rytov_limit,
+                           int max_screens, double* dz_out, double* cn2_out, double* rytov_out, int* n_out);
+
 /* Raw Philox4x32-10 words (Salmon et al., SC'11) of n counters, for bit-exact checks of the noise
  * generator used by the screens: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key).  ctr and out
  * are device uint32 arrays of 4n words. */

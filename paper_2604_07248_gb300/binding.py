@@ -64,6 +64,9 @@ SIGNATURES = {
                             C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
+    "ts_cn2_hufnagel_valley": (_I, [_P, _I, _D, _D, _P]),
+    "ts_rytov_interval": (_I, [_P, _P, _I, _D, _D, _D, _P]),
+    "ts_place_screens": (_I, [_P, _P, _I, C.POINTER(Medium), C.POINTER(Grid), _D, _P, _I, _D, _I, _P, _P, _P, _P]),
     "ts_plan_set_sources": (_I, [_P, _I, _P]),
     "ts_make_sources": (_I, [_P, _P, _I, _P]),
     "ts_make_screens": (_I, [_P, _U64, _U32, _I, _P, _P, _P]),
@@ -138,6 +141,49 @@ def _stream(stream) -> int | None:
 def max_step(lam, N, dx, n0=1.0) -> float:
     """Eq. 7 aliasing-limited step [m] for this wavelength and grid."""
     return load().ts_max_step(C.byref(Medium(lam, n0, 0.0, 0.0)), C.byref(Grid(N, dx)))
+
+
+def _host_f64(x):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def cn2_hufnagel_valley(h, V=21.0, A=1.7e-14):
+    """Hufnagel-Valley Cn^2 (S21) at heights h [m] (HV5/7: V = 21 m/s, A = 1.7e-14); numpy array."""
+    import numpy as np
+    ha, hp = _host_f64(np.atleast_1d(h))
+    out = np.zeros_like(ha)
+    _check(load().ts_cn2_hufnagel_valley(hp, int(ha.size), float(V), float(A), out.ctypes.data_as(C.c_void_p)),
+           "ts_cn2_hufnagel_valley")
+    return out
+
+
+def rytov_interval(prof_z, prof_cn2, lam, z0, z1) -> float:
+    """Rytov variance (S19) of [z0, z1] for a piecewise-linear sampled Cn^2 profile."""
+    za, zp = _host_f64(prof_z)
+    ca, cp = _host_f64(prof_cn2)
+    out = C.c_double()
+    _check(load().ts_rytov_interval(zp, cp, int(za.size), float(lam), float(z0), float(z1), C.byref(out)),
+           "ts_rytov_interval")
+    return out.value
+
+
+def place_screens(prof_z, prof_cn2, lam, N, dx, L, rytov_limit, init_bounds=None, max_screens=64, n0=1.0):
+    """Screen placement of Sec. 2.4 (see ts_place_screens): returns numpy arrays (dz, cn2, rytov)."""
+    import numpy as np
+    za, zp = _host_f64(prof_z)
+    ca, cp = _host_f64(prof_cn2)
+    ib = np.zeros(0) if init_bounds is None else np.asarray(init_bounds, dtype=np.float64)
+    ia, ip = _host_f64(ib)
+    dz, cn, ry = (np.zeros(int(max_screens)) for _ in range(3))
+    n = C.c_int()
+    _check(load().ts_place_screens(zp, cp, int(za.size), C.byref(Medium(lam, n0, 0.0, 0.0)), C.byref(Grid(N, dx)),
+                                   float(L), ip if ia.size else None, int(ia.size), float(rytov_limit),
+                                   int(max_screens), dz.ctypes.data_as(C.c_void_p), cn.ctypes.data_as(C.c_void_p),
+                                   ry.ctypes.data_as(C.c_void_p), C.byref(n)), "ts_place_screens")
+    k = n.value
+    return dz[:k].copy(), cn[:k].copy(), ry[:k].copy()
 
 
 def philox4x32_10(ctr, key0, key1, out, stream=None):
