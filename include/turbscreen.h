@@ -222,12 +222,19 @@ ts_status ts_moments_accumulate(ts_plan plan, const float* intensity, int B, int
 ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2, int n_groups, int64_t count,
                               double* si_map, double* si_mean, double* si_center, void* stream);
 
+/* Factor applied to the D2NN receiver loss and to all its gradients (default 1): e.g. 1 / max(Iref)
+ * for the MAE (kind 0) or 1 / max(Iref)^2 for the squared error normalises the intensities to the
+ * reference's peak, which keeps the mask gradients of a unit-amplitude source in the range an Adam
+ * optimiser with eps = 1e-8 resolves.  Host-side setting of the plan; later calls use it. */
+ts_status ts_plan_set_loss_scale(ts_plan plan, double scale);
+
 /* Two-mask dual-domain D2NN receiver (Sec. 2.5, 4.1), batch of B fields U (device complex64):
  *   Z1 = exp(i th1) A U;  W2 = exp(i th2) C(Z1);  V = C^-1(W2);  I = |V|^2,
  * C = fftshift o FFT2 o ifftshift / N (lens as a unitary centred DFT), A = disk of diameter
  * `aperture` [m] centred on pixel (N/2, N/2).  Loss against the reference intensity Iref
  * (device float32 [N][N]): kind 0 = mean |I - Iref| (MAE, Sec. 2.5), kind 1 = mean (I - Iref)^2,
- * mean over batch and pixels; written to loss (device float64 [1]).
+ * mean over batch and pixels, times the plan's loss scale (ts_plan_set_loss_scale); written to loss
+ * (device float64 [1]).
  * th1, th2: device float32 [N][N].  ws: device complex64 workspace [3][B][N][N] kept for the
  * backward call (Z1, W2, V); intensity: device float32 [B][N][N], written (also kept for the
  * backward call).  B <= max_batch.  N must be divisible by 4 (all supported N are). */
@@ -264,6 +271,12 @@ ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* tot
  * err: device int, set to nonzero if the wait for the MMAs ran out of timeout_s. */
 ts_status ts_tc_dft32(const void* x, void* X, int nvec, int sign, int layout, double timeout_s, int* err,
                       void* stream);
+
+/* Adam step of the D2NN training loop (Sec. 2.5; Kingma & Ba 2015), elementwise over n device
+ * floats: m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2; p <- p - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * param, m, v: device float32 [n] in/out; grad: device float32 [n]; t >= 1 is the step number. */
+ts_status ts_adam_step(float* param, const float* grad, float* m, float* v, long long n, double lr, double beta1,
+                       double beta2, double eps, int t, void* stream);
 
 /* ---- path planning (host functions, no GPU) ---------------------------------------------------- */
 

@@ -59,12 +59,14 @@ SIGNATURES = {
     "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
     "ts_plan_destroy": (_I, [_P]),
     "ts_plan_device_status": (_I, [_P]),
+    "ts_plan_set_loss_scale": (_I, [_P, _D]),
     "ts_plan_device_bytes": (C.c_size_t, [_P]),
     "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_cn2_hufnagel_valley": (_I, [_P, _I, _D, _D, _P]),
+    "ts_adam_step": (_I, [_P, _P, _P, _P, C.c_longlong, _D, _D, _D, _D, _I, _P]),
     "ts_rytov_interval": (_I, [_P, _P, _I, _D, _D, _D, _P]),
     "ts_place_screens": (_I, [_P, _P, _I, C.POINTER(Medium), C.POINTER(Grid), _D, _P, _I, _D, _I, _P, _P, _P, _P]),
     "ts_plan_set_sources": (_I, [_P, _I, _P]),
@@ -141,6 +143,12 @@ def _stream(stream) -> int | None:
 def max_step(lam, N, dx, n0=1.0) -> float:
     """Eq. 7 aliasing-limited step [m] for this wavelength and grid."""
     return load().ts_max_step(C.byref(Medium(lam, n0, 0.0, 0.0)), C.byref(Grid(N, dx)))
+
+
+def adam_step(param, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on device float32 tensors (see ts_adam_step); t >= 1."""
+    _check(load().ts_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()), float(lr), float(beta1),
+                               float(beta2), float(eps), int(t), _stream(stream)), "ts_adam_step")
 
 
 def _host_f64(x):
@@ -255,6 +263,10 @@ class Plan:
         _check(load().ts_plan_tuning(self._h, C.byref(e), C.byref(a), C.byref(b), C.byref(g), us, C.byref(v),
                                      C.byref(w), C.byref(rv), C.byref(rw)), "ts_plan_tuning")
         return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]], v.value, w.value, rv.value, rw.value
+
+    def set_loss_scale(self, scale: float):
+        """Factor on the D2NN receiver loss and its gradients (see ts_plan_set_loss_scale)."""
+        _check(load().ts_plan_set_loss_scale(self._h, float(scale)), "ts_plan_set_loss_scale")
 
     def device_status(self):
         """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a tensor-core wait of a

@@ -601,6 +601,14 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
     return TS_OK;
 }
 
+ts_status ts_plan_set_loss_scale(ts_plan plan, double scale)
+{
+    if (!plan || !(scale > 0.0) || !std::isfinite(scale))
+        return fail(TS_ERR_INVALID_ARG, "ts_plan_set_loss_scale: need a plan and a finite scale > 0");
+    reinterpret_cast<Plan*>(plan)->loss_scale = scale;
+    return TS_OK;
+}
+
 ts_status ts_plan_device_status(ts_plan plan)
 {
     if (!plan) return fail(TS_ERR_INVALID_ARG, "ts_plan_device_status: null plan");

@@ -295,7 +295,7 @@ cudaError_t launch_d2nn(const Plan& p, bool backward, const D2nnArgs& d, cudaStr
     a.tw = p.tw;
     const double rad = 0.5 * d.aperture / p.dx;
     a.r2ap = (float)(rad * rad);
-    a.inv_count = (float)(1.0 / ((double)d.B * (double)N2));
+    a.inv_count = (float)(p.loss_scale / ((double)d.B * (double)N2));
     a.kind = d.kind;
     cudaError_t e = cudaSuccess;
     switch (N) {
@@ -309,7 +309,8 @@ cudaError_t launch_d2nn(const Plan& p, bool backward, const D2nnArgs& d, cudaStr
     if (e != cudaSuccess) return e;
     if (!backward) {
         const int per_row = (N == 2048) ? 2 : 1;  // one partial per warp of a line
-        loss_sum_kernel<<<1, 256, 0, st>>>(p.ws_rows, d.B * N * per_row, 1.0 / ((double)d.B * (double)N2), d.loss);
+        loss_sum_kernel<<<1, 256, 0, st>>>(p.ws_rows, d.B * N * per_row, p.loss_scale / ((double)d.B * (double)N2),
+                                           d.loss);
     } else {
         const unsigned grid = (unsigned)((N2 + 255) / 256);
         batch_sum_kernel<<<grid, 256, 0, st>>>(a.z1, d.B, N2, d.g_th1);

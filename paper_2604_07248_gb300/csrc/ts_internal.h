@@ -27,6 +27,7 @@ struct Plan {
     double cn2[kMaxScreens] = {};
     int n_src = 0;
     float src_coef[kMaxSources] = {};  // dx^2 / w0^2, or -1 for a plane wave
+    double loss_scale = 1.0;           // factor on the D2NN receiver loss and its gradients
 
     // device tables (FP64-built, FP32-stored unless noted)
     float2* tw = nullptr;      // Stockham stage twiddles, forward sign (default E for N)
