@@ -82,6 +82,9 @@ typedef struct ts_plan_s* ts_plan;
                                     BF16 hi + lo (products hi.hi + hi.lo + lo.hi, about 2^-16 relative
                                     error per stage).  N = 1024 only (else TS_ERR_UNSUPPORTED).  Screens,
                                     moments and the D2NN receiver stay FP32.  Not accepted by ts_batch. */
+#define TS_PLAN_TEST_STALL 4     /* test hook: the prefetching passes (column / row variant 2) never issue their
+                                  * first copy, so their first bounded wait runs out (budget 50 ms instead of
+                                  * one second) and ts_plan_device_status reports TS_ERR_DEVICE_TIMEOUT */
 
 /* Creates a plan for one medium, grid and path.  sh_levels is 0 or 3 (subharmonic levels, Eq. 2,
  * scale factor 3).  max_batch bounds the number of fields per ts_propagate / ts_propagate_backward
@@ -96,10 +99,11 @@ typedef struct ts_plan_s* ts_plan;
 ts_status ts_plan_create(ts_plan* plan, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
                          int sh_levels, int max_batch, int flags);
 
-/* Device status of a TS_PLAN_SPLIT_BF16 plan: waits for all work on the device, then returns
- * TS_ERR_DEVICE_TIMEOUT (and clears the flag) if a wait of its tensor-core passes for their MMAs ran
- * out of its one-second budget since the last call -- the pass then stopped early and its output is
- * incomplete -- else TS_OK.  Plans without the flag always return TS_OK. */
+/* Device status of a plan: waits for all work on the device, then returns TS_ERR_DEVICE_TIMEOUT
+ * (and clears the flag) if a bounded device wait of its passes ran out of its one-second budget since
+ * the last call -- a tensor-core pass (TS_PLAN_SPLIT_BF16) waiting for its MMAs, or a prefetching
+ * pass (column / row variant 2) waiting for its TMA copy; the pass then stopped early and its output
+ * is incomplete -- else TS_OK. */
 ts_status ts_plan_device_status(ts_plan plan);
 
 /* Frees the plan's device memory (synchronises the device).  NULL is accepted. */
@@ -124,6 +128,17 @@ size_t ts_plan_device_bytes(ts_plan plan);
 ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
                          float* us_streams, int* col_variant, float* us_e32_warp_columns, int* row_variant,
                          float* us_e32_shared_phasor_rows);
+
+/* The autotuner's whole candidate table: *n receives the number of candidates (7); for the first
+ * min(max, *n) of them, points_per_thread[c] (16 or 32), col_variant[c] (0: a column line shared by
+ * four warps; 1: one warp per column, tile staged through shared memory; 2: persistent CTAs whose next
+ * 8-column tile arrives by TMA while the current one is transformed), row_variant[c] (0: each CTA
+ * reads its screen rows; 1: phasor rows shared by the CTA's fields; 2: persistent warps that prefetch
+ * their next field row and the screen phasor row with bulk asynchronous copies) and us[c], the timed
+ * cost in microseconds of one column + one row pass (0 = not timed).  Variants 1 and 2 exist for
+ * N = 1024 at 32 points per thread.  Output arrays may be NULL.  Host-only; no device work. */
+ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
+                                    int* row_variant, float* us);
 
 /* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
  * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */

@@ -22,6 +22,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "aliasing (Eq. 7)", 3: "workspace",
 
 TS_PLAN_ALLOW_ALIASING = 1
 TS_PLAN_SPLIT_BF16 = 2
+TS_PLAN_TEST_STALL = 4
 TS_PROP_SOURCE = 1
 TS_PROP_INTENSITY = 2
 TS_PROP_NO_FIELD = 4
@@ -64,6 +65,7 @@ SIGNATURES = {
     "ts_plan_tuning": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "ts_plan_tuning_candidates": (_I, [_P, _I, C.POINTER(C.c_int), _P, _P, _P, _P]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_cn2_hufnagel_valley": (_I, [_P, _I, _D, _D, _P]),
     "ts_adam_step": (_I, [_P, _P, _P, _P, C.c_longlong, _D, _D, _D, _D, _I, _P]),
@@ -264,13 +266,26 @@ class Plan:
                                      C.byref(w), C.byref(rv), C.byref(rw)), "ts_plan_tuning")
         return e.value, a.value, b.value, g.value, [us[0], us[1], us[2]], v.value, w.value, rv.value, rw.value
 
+    def tuning_candidates(self):
+        """The autotuner's candidate table: a list of (points per thread, column variant, row variant,
+        us for one column + one row pass; 0 = not timed)."""
+        n = C.c_int()
+        _check(load().ts_plan_tuning_candidates(self._h, 0, C.byref(n), None, None, None, None),
+               "ts_plan_tuning_candidates")
+        e, cv, rv = (C.c_int * n.value)(), (C.c_int * n.value)(), (C.c_int * n.value)()
+        us = (C.c_float * n.value)()
+        _check(load().ts_plan_tuning_candidates(self._h, n.value, C.byref(n), e, cv, rv, us),
+               "ts_plan_tuning_candidates")
+        return [(e[i], cv[i], rv[i], us[i]) for i in range(n.value)]
+
     def set_loss_scale(self, scale: float):
         """Factor on the D2NN receiver loss and its gradients (see ts_plan_set_loss_scale)."""
         _check(load().ts_plan_set_loss_scale(self._h, float(scale)), "ts_plan_set_loss_scale")
 
     def device_status(self):
-        """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a tensor-core wait of a
-        TS_PLAN_SPLIT_BF16 plan ran out of its budget since the last call."""
+        """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a bounded device wait of
+        the plan's passes (tensor-core MMAs, or the TMA copies of the prefetching variants) ran out of its
+        budget since the last call."""
         _check(load().ts_plan_device_status(self._h), "ts_plan_device_status")
 
     def close(self):

@@ -211,8 +211,8 @@ ts_status autotune(Plan& p)
     if (const char* env = std::getenv("TS_FFT_E")) force_e = std::atoi(env);
     if (const char* env = std::getenv("TS_COL_VARIANT")) force_v = std::atoi(env);
     if (const char* env = std::getenv("TS_ROW_VARIANT")) force_r = std::atoi(env);
-    constexpr int kCand = 4;
-    const int cand_e[kCand] = {16, 32, 32, 32}, cand_v[kCand] = {0, 0, 1, 0}, cand_r[kCand] = {0, 0, 0, 1};
+    constexpr int kCand = kTuneCand;
+    const int *cand_e = kCandE, *cand_v = kCandCol, *cand_r = kCandRow;
     bool use[kCand];
     int n_use = 0, only = -1;
     for (int c = 0; c < kCand; ++c) {
@@ -463,14 +463,16 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     // separable transfer function when the dropped terms are negligible for every step:
     // dz kappa^6 / 16k^5 <= 1e-7 rad and the cross term dz kx^2 ky^2 / 4k^3 <= 0.05 rad
     {
-        bool sep = true;
+        bool sep = true, tiny = true;
         const double kx2 = std::pow(M_PI / grid->dx, 2.0), k = tmp.k;
         for (int s = 0; s < tmp.S; ++s) {
             const double r6 = tmp.dz[s] * kap2max * kap2max * kap2max / (16.0 * std::pow(k, 5.0));
             const double ex = tmp.dz[s] * kx2 * kx2 / (4.0 * k * k * k);
             if (r6 > 1e-7 || ex > 0.05) sep = false;
+            if (ex > 0.01) tiny = false;  // exp(-i e) to second order: error e^3 / 6 <= 1.7e-7 rad
         }
         tmp.sep_transfer = sep;
+        tmp.tiny_cross = sep && tiny;
     }
 
     Plan* p = new Plan(tmp);
@@ -506,12 +508,17 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     p->regen_all = (size_t)max_batch * S * N2 * sizeof(float2) <= (256ull << 20);
     ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * (p->regen_all ? S : 1) * N2));
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
-    if (p->split_bf16) {
-        ok(dalloc(*p, &p->d_err, 1));
-        if (p->d_err) ok(cudaMemset(p->d_err, 0, sizeof(int)));
+    // device error word and wait budget of the passes with bounded waits (tensor-core and prefetching passes)
+    ok(dalloc(*p, &p->d_err, 1));
+    if (p->d_err) ok(cudaMemset(p->d_err, 0, sizeof(int)));
+    {
         int khz = 0;
         ok(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, p->device));
-        p->tc_budget = (long long)(1.0 * (double)(khz > 0 ? khz : 2000000) * 1e3);  // one second
+        p->test_stall = (flags & TS_PLAN_TEST_STALL) != 0;
+        const double seconds = p->test_stall ? 0.05 : 1.0;
+        p->tc_budget = (long long)(seconds * (double)(khz > 0 ? khz : 2000000) * 1e3);
+    }
+    if (p->split_bf16) {
         // column tiles of 4 columns (one 128-vector group) unless TS_TC_COL_GROUPS=2 asks for 8
         const char* env = std::getenv("TS_TC_COL_GROUPS");
         p->tc_col_groups = (env && std::atoi(env) == 2) ? 2 : 1;
@@ -601,6 +608,21 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
     return TS_OK;
 }
 
+ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
+                                    int* row_variant, float* us)
+{
+    if (!plan || !n) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning_candidates: need plan and n");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    *n = kTuneCand;
+    for (int c = 0; c < kTuneCand && c < max; ++c) {
+        if (points_per_thread) points_per_thread[c] = kCandE[c];
+        if (col_variant) col_variant[c] = kCandCol[c];
+        if (row_variant) row_variant[c] = kCandRow[c];
+        if (us) us[c] = p->tune_us[c];
+    }
+    return TS_OK;
+}
+
 ts_status ts_plan_set_loss_scale(ts_plan plan, double scale)
 {
     if (!plan || !(scale > 0.0) || !std::isfinite(scale))
@@ -619,7 +641,7 @@ ts_status ts_plan_device_status(ts_plan plan)
     if (e == cudaSuccess) e = cudaMemcpy(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && code != 0) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_device_status");
-    if (code != 0) return fail(TS_ERR_DEVICE_TIMEOUT, "a tensor-core wait of the plan ran out of its budget");
+    if (code != 0) return fail(TS_ERR_DEVICE_TIMEOUT, "a bounded device wait of the plan (tensor-core or prefetching pass) ran out of its budget");
     return TS_OK;
 }
 

@@ -15,6 +15,13 @@ constexpr int kMaxSources = 64;
 constexpr int kShCoef = 27;     // 3 levels x 9 sub-grid cells (cell 4 = DC, unused)
 constexpr int kShVectors = 7;   // V0, (Vc_p, Vs_p) for p = 1..3
 
+// autotuner candidates of the propagation passes: (points per thread, column variant, row variant);
+// variants other than 0 exist for N = 1024 at 32 points per thread
+constexpr int kTuneCand = 7;
+constexpr int kCandE[kTuneCand] = {16, 32, 32, 32, 32, 32, 32};
+constexpr int kCandCol[kTuneCand] = {0, 0, 1, 0, 2, 0, 2};
+constexpr int kCandRow[kTuneCand] = {0, 0, 0, 1, 0, 2, 2};
+
 struct Plan {
     int device = 0;
     int N = 0;
@@ -35,18 +42,21 @@ struct Plan {
     int fft_e = 32;            // points per thread of the propagation passes (16 or 32; 16 for N <= 256)
     bool split_bf16 = false;   // propagation passes on the tensor cores (split-BF16 DFTs, N = 1024)
     int* d_err = nullptr;      // device error word of the tensor-core passes (nonzero after a timeout)
-    long long tc_budget = 0;   // clock64 cycles a tensor-core wait may take
+    long long tc_budget = 0;   // clock64 cycles a bounded device wait may take (tensor-core and prefetching passes)
+    bool test_stall = false;   // TS_PLAN_TEST_STALL: prefetching passes skip their first copy
     int tc_col_groups = 1;     // tensor-core column tiles: 1 = 4 columns (4 CTAs / SM), 2 = 8 columns (2 CTAs / SM)
-    int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column (N = 1024, E = 32)
-    int row_variant = 0;       // row pass: 0 = per-CTA screen rows, 1 = phasor rows shared by the CTA's fields
-    float tune_us[4] = {0, 0, 0, 0};  // autotuner timings of one column + row pass per candidate (E, col, row):
-                                      // (16,0,0), (32,0,0), (32,1,0), (32,0,1)
+    int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column, 2 = persistent
+                               // CTAs with TMA-prefetched tiles (1 and 2: N = 1024, E = 32)
+    int row_variant = 0;       // row pass: 0 = per-CTA screen rows, 1 = phasor rows shared by the CTA's fields,
+                               // 2 = persistent warps with bulk-copy prefetch of rows and phasor rows
+    float tune_us[8] = {};     // autotuner timings of one column + row pass per candidate (kCandE/Col/Row)
     int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)
     bool sep_transfer = false; // P includes the kappa^4 / 8k^3 term and kernels add the kx^2 ky^2 cross term
+    bool tiny_cross = false;   // separable, and the cross term stays <= 0.01 rad on the whole grid
     float* dcoef = nullptr;    // [S] dz / (2 k^3)  (non-paraxial phase correction)
     float* amp = nullptr;      // [S] sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
     float* g = nullptr;        // [N][N] (kappa^2 + kappa0^2)^(-11/12) exp(-kappa^2 / 2 kappa_m^2), g(0) = 0

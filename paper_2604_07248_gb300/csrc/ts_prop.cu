@@ -33,7 +33,7 @@ __global__ void row_sums_kernel(const double* rows, int B, int N, int wpl, doubl
 
 cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStream_t st)
 {
-    RowParams rp;
+    RowParams rp{};
     rp.field = a.field;
     rp.phi = a.phi;
     rp.phasor = a.phasor;
@@ -48,6 +48,9 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
     rp.n_src = p.n_src > 0 ? p.n_src : 1;
     for (int i = 0; i < kMaxSources; ++i) rp.src_coef[i] = i < p.n_src ? p.src_coef[i] : -1.0f;
     rp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
+    rp.err = p.d_err;
+    rp.budget = p.tc_budget;
+    rp.stall = p.test_stall ? 1 : 0;
     if (p.split_bf16) return tc_row_pass(flags, rp, a.B, p.tc_budget, p.d_err, st);
     switch (p.N) {
     case 128: return row_pass_n<128>(p.fft_e, p.row_variant, flags, rp, a.B, st);
@@ -61,7 +64,7 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
 
 cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st)
 {
-    ColParams cp;
+    ColParams cp{};
     cp.field = field;
     cp.tw = p.tw;
     cp.P = p.P + (size_t)step * p.N;
@@ -70,6 +73,10 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
     cp.inv_k2 = (float)(1.0 / (p.k * p.k));
     cp.dk = (float)p.dk;
     cp.tw = p.fft_e == 16 ? p.tw16 : p.tw;
+    cp.err = p.d_err;
+    cp.budget = p.tc_budget;
+    cp.tiny_cross = p.tiny_cross;
+    cp.stall = p.test_stall ? 1 : 0;
     if (p.split_bf16) return tc_col_pass(p.tc_col_groups, conj, p.sep_transfer, cp, B, p.tc_budget, p.d_err, st);
     switch (p.N) {
     case 128: return col_pass_n<128>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
@@ -83,6 +90,10 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
 
 cudaError_t prepare_prop_kernels(int N)
 {
+    if (N == 1024) {
+        cudaError_t e = prepare_prop_tma_1024();
+        if (e != cudaSuccess) return e;
+    }
     switch (N) {
     case 128: return prepare_prop_n<128>();
     case 256: return prepare_prop_n<256>();

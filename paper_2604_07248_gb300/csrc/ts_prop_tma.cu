@@ -1,0 +1,433 @@
+// ts_prop_tma.cu -- persistent propagation passes for N = 1024 that prefetch their next input with the
+// Tensor Memory Accelerator while the current one is transformed (Eq. 1: column pass FFT -> H -> IFFT,
+// row pass IFFT -> exp(i phi) -> FFT).
+//
+// Column pass: a CTA of 256 threads owns 8-column tiles (64 KiB: 1024 rows x 64 bytes).  Tile k+1 is
+// loaded by four 2-D tensor copies (boxes of 256 rows x 16 floats) into the CTA's exchange buffer as
+// soon as the last exchange of tile k has been read, so the load runs under the last radix-32 stage
+// and the stores of tile k.  Thread (t, c) = (tid / 8, tid % 8) holds points t + 32 i of column c.
+//
+// Row pass: every warp owns one 1024-point row at a time and its own 8 KiB line buffer, with its own
+// mbarrier: the phasor row of the step is bulk-copied into the line buffer while the second stage of
+// the inverse FFT runs, and the warp's next field row while the second stage of the forward FFT runs.
+// Warps never wait for one another after the twiddles are staged.
+//
+// Every wait on an mbarrier is bounded by the plan's clock64 budget; a wait that runs out sets the
+// plan's error word (read by ts_plan_device_status) and the CTA (column pass) or warp (row pass)
+// returns after a second bounded wait for its copy in flight.
+#include <cuda.h>
+
+#include "ts_device.cuh"
+#include "ts_prop_decl.h"
+
+namespace ts {
+namespace {
+
+constexpr int kN = 1024;
+constexpr int kErrTmaWait = 4;  // error word value: a prefetch wait ran out of its budget
+
+__device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, long long budget)
+{
+    if (mbar_try(m, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(m, parity)) {
+        if (clock64() - t0 > budget) return false;
+    }
+    return true;
+}
+// generic-proxy accesses of this thread (and those ordered before it by a barrier) before later
+// asynchronous-proxy accesses of shared memory
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 2-D tiled tensor copy global -> shared, completion counted in bytes on the mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            s32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(s32(m))
+        : "memory");
+}
+// contiguous bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s32(dst)),
+                 "l"(src), "r"(bytes), "r"(s32(m))
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// column pass
+// ---------------------------------------------------------------------------------------------
+struct ColTma {
+    using C = FftCfg<kN, 32>;  // 32 threads per column, 32 points each, stages 32 x 32
+    static constexpr int W = 8, THREADS = 256, BOX_ROWS = 256;
+    static constexpr int TPF = kN / W;                       // tiles per field
+    static constexpr int LS = C::padded + 2;                 // column stride of the exchange buffer
+    static constexpr int TILE_BYTES = W * kN * 8;            // 64 KiB
+    static constexpr size_t off_ht = sizeof(float2) * C::tw_smem;
+    static constexpr size_t off_buf = off_ht + sizeof(float4) * kN;
+    static constexpr size_t off_bar = off_buf + sizeof(float2) * W * LS;
+    static constexpr size_t smem = off_bar + 16;
+    static_assert(W * LS >= W * kN, "the dense tile fits the exchange buffer");
+    static_assert(off_buf % 128 == 0, "TMA destination alignment");
+};
+
+// v[i] (frequency m = t + 32 i of column col) *= H or conj(H).  ht[m] = (P(m), ky(m)^2).
+// HMODE 0: exact angular-spectrum phase beyond its paraxial part; 1: separable P' with the cross term
+// exp(-i e) as a short series; 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
+template <bool CONJ, int HMODE>
+__device__ __forceinline__ void transfer_tile(float2 (&v)[32], const ColParams& a, const float4* ht, int col, int t)
+{
+    const float4 hx = ht[col];
+    const float2 px = make_float2(hx.x, hx.y);
+    const float kx2 = hx.z;
+    const float cx = a.ccross * kx2;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float4 hy = ht[t + 32 * i];
+        const float2 q = cmul(px, make_float2(hy.x, hy.y));
+        float2 h;
+        if constexpr (HMODE == 0) {
+            const float k2 = kx2 + hy.z;
+            const float qq = k2 * a.inv_k2;
+            if (qq >= 1.0f) {
+                h = make_float2(0.0f, 0.0f);
+            } else {
+                const float d = 1.0f + sqrtf(1.0f - qq);
+                const float del = __fdividef(a.dcoef * k2 * k2, d * d);
+                const float d2 = del * del;
+                const float cd = 1.0f - d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+                const float sd = del * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f - d2 * (1.0f / 5040.0f))));
+                h = cmul(q, make_float2(cd, -sd));
+            }
+        } else if constexpr (HMODE == 1) {
+            const float e = cx * hy.z;
+            const float e2 = e * e;
+            h = cmul(q, make_float2(1.0f - e2 * (0.5f - e2 * (1.0f / 24.0f)), -e * (1.0f - e2 * (1.0f / 6.0f))));
+        } else {
+            const float e = cx * hy.z;
+            const float ce = fmaf(-0.5f * e, e, 1.0f);
+            h = make_float2(fmaf(q.x, ce, q.y * e), fmaf(q.y, ce, -q.x * e));
+        }
+        v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+    }
+}
+
+template <bool CONJ, int HMODE>
+__global__ void __launch_bounds__(ColTma::THREADS, 2)
+    col_pass_tma_kernel(const ColParams a, const __grid_constant__ CUtensorMap tmap, int B)
+{
+    using C = ColTma::C;
+    constexpr int W = ColTma::W, TPF = ColTma::TPF;
+    extern __shared__ __align__(128) unsigned char sm[];
+    float2* tw = reinterpret_cast<float2*>(sm);
+    float4* ht = reinterpret_cast<float4*>(sm + ColTma::off_ht);
+    float2* buf = reinterpret_cast<float2*>(sm + ColTma::off_buf);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + ColTma::off_bar);
+    const int tid = threadIdx.x, c = tid % W, t = tid / W;
+    const int tiles = B * TPF;
+    int tile = blockIdx.x;
+    if (tile >= tiles) return;  // uniform over the CTA
+    auto issue = [&](int tl) {  // one thread: the four boxes of tile tl
+        const int b = tl / TPF, x = 2 * (tl % TPF) * W;
+        mbar_expect_tx(bar, ColTma::TILE_BYTES);
+#pragma unroll
+        for (int q = 0; q < kN / ColTma::BOX_ROWS; ++q)
+            tma_load_2d(buf + q * ColTma::BOX_ROWS * W, &tmap, x, b * kN + q * ColTma::BOX_ROWS, bar);
+    };
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        if (!a.stall) issue(tile);
+    }
+    stage_twiddles_c<C>(tw, a.tw);
+    for (int i = tid; i < kN; i += ColTma::THREADS) {
+        const float2 p = __ldg(a.P + i);
+        const float k = a.dk * (float)kidx(i, kN);
+        ht[i] = make_float4(p.x, p.y, k * k, 0.0f);
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (; tile < tiles; tile += gridDim.x, parity ^= 1u) {
+        const int b = tile / TPF, col = (tile % TPF) * W + c;
+        const bool ok = mbar_wait(bar, parity, a.budget);
+        float2 v[32];
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = buf[(t + 32 * i) * W + c];
+        }
+        if (__syncthreads_or(!ok)) {  // every thread has read the tile before the exchange reuses it
+            if (tid == 0) {
+                atomicExch(a.err, kErrTmaWait);
+                mbar_wait(bar, parity, a.budget);  // the copy in flight, bounded again
+            }
+            return;
+        }
+        float2* line = buf + c * ColTma::LS;
+        fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
+        fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
+        transfer_tile<CONJ, HMODE>(v, a, ht, col, t);
+        fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
+        if (tid == 0 && tile + (int)gridDim.x < tiles) {
+            fence_proxy_async();
+            issue(tile + gridDim.x);
+        }
+        fft_stage_c<C, 1, +1>(v, line, t, tw, BlockBar());
+        float2* base = a.field + (size_t)b * kN * kN + col;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) base[(size_t)(t + 32 * i) * kN] = v[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// row pass
+// ---------------------------------------------------------------------------------------------
+struct RowTma {
+    using C = FftCfg<kN, 32>;  // one warp per row
+    static constexpr int WARPS = 8, THREADS = 32 * WARPS;
+    static constexpr int LS = C::padded;  // line stride (float2); a line holds the dense row or the exchange
+    static constexpr int ROW_BYTES = kN * 8;
+    static constexpr size_t off_line = sizeof(float2) * C::tw_smem;
+    static constexpr size_t off_bar = off_line + sizeof(float2) * WARPS * LS;
+    static constexpr size_t smem = off_bar + 8 * WARPS;
+    static_assert(off_line % 128 == 0 && (sizeof(float2) * LS) % 16 == 0, "bulk-copy destination alignment");
+};
+
+template <int FLAGS>
+__global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const RowParams a, int B, int per_warp)
+{
+    using C = RowTma::C;
+    static_assert((FLAGS & RP_IN_FREQ) && (FLAGS & RP_PHASOR) && (FLAGS & RP_STORE) && !(FLAGS & RP_INTENSITY) &&
+                      !(FLAGS & RP_IN_SOURCE),
+                  "row pass of a step in the row-frequency domain");
+    extern __shared__ __align__(128) unsigned char sm[];
+    float2* tw = reinterpret_cast<float2*>(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* line = reinterpret_cast<float2*>(sm + RowTma::off_line) + warp * RowTma::LS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RowTma::off_bar) + warp;
+    const int rows = B * kN;
+    // rows gw * per_warp .. + per_warp - 1 of the launch (consecutive rows of one field share phasor sets)
+    const int gw = blockIdx.x * RowTma::WARPS + warp;
+    const int r0 = gw * per_warp, r1 = min(rows, r0 + per_warp);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        if (r0 < r1 && !a.stall) {
+            mbar_expect_tx(bar, RowTma::ROW_BYTES);
+            bulk_load(line, a.field + (size_t)r0 * kN, RowTma::ROW_BYTES, bar);
+        }
+    }
+    stage_twiddles_c<C>(tw, a.tw);
+    __syncthreads();
+    uint32_t parity = 0;
+    for (int r = r0; r < r1; ++r) {
+        const int b = r / kN, j = r % kN;
+        float2 v[32];
+        if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, a.budget))) {
+            if (lane == 0) {
+                atomicExch(a.err, kErrTmaWait);
+                mbar_wait(bar, parity, a.budget);  // the copy in flight, bounded again
+            }
+            return;
+        }
+        parity ^= 1u;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = line[lane + 32 * i];
+        __syncwarp();  // every lane has its points before the exchange overwrites the row
+        fft_stage_c<C, 0, +1>(v, line, lane, tw, WarpBar());
+        if (lane == 0) {  // the line is free: the step's screen phasor row comes in under the next stage
+            const int set = (b + a.phi_off) / a.phi_group;
+            fence_proxy_async();
+            mbar_expect_tx(bar, RowTma::ROW_BYTES);
+            bulk_load(line, a.phasor + (long long)set * a.phi_set_stride + (size_t)j * kN, RowTma::ROW_BYTES, bar);
+        }
+        fft_stage_c<C, 1, +1>(v, line, lane, tw, WarpBar());
+        if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, a.budget))) {
+            if (lane == 0) {
+                atomicExch(a.err, kErrTmaWait);
+                mbar_wait(bar, parity, a.budget);
+            }
+            return;
+        }
+        parity ^= 1u;
+        if (a.phase_sign > 0.0f) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = cmul(v[i], line[lane + 32 * i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = cmulc(v[i], line[lane + 32 * i]);
+        }
+        __syncwarp();
+        if constexpr (FLAGS & RP_OUT_FREQ) {
+            fft_stage_c<C, 0, -1>(v, line, lane, tw, WarpBar());
+            if (lane == 0 && r + 1 < r1) {
+                fence_proxy_async();
+                mbar_expect_tx(bar, RowTma::ROW_BYTES);
+                bulk_load(line, a.field + (size_t)(r + 1) * kN, RowTma::ROW_BYTES, bar);
+            }
+            fft_stage_c<C, 1, -1>(v, line, lane, tw, WarpBar());
+        } else {
+            if (lane == 0 && r + 1 < r1) {
+                fence_proxy_async();
+                mbar_expect_tx(bar, RowTma::ROW_BYTES);
+                bulk_load(line, a.field + (size_t)(r + 1) * kN, RowTma::ROW_BYTES, bar);
+            }
+        }
+        float2* row = a.field + (size_t)r * kN;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) row[lane + 32 * i] = v[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    return fn;
+}
+
+// CTAs resident per SM for a kernel (cached per kernel address and device)
+template <class K>
+int max_ctas(K kernel, int threads, size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) return 0;
+    return sms * per;
+}
+
+// a balanced persistent grid: the fewest CTAs that keep every CTA's share of the work units at the
+// share a full-residency grid would need
+inline int balanced_grid(int units, int resident, int* per)
+{
+    const int p = (units + resident - 1) / resident;
+    *per = p;
+    return (units + p - 1) / p;
+}
+
+template <bool CONJ, int HMODE>
+cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * kN, (cuuint64_t)B * kN};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * kN * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * ColTma::W), (cuuint32_t)ColTma::BOX_ROWS};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, cp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    static int resident = 0;
+    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE>, ColTma::THREADS, ColTma::smem);
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    int per = 0;
+    const int grid = balanced_grid(B * ColTma::TPF, resident, &per);
+    col_pass_tma_kernel<CONJ, HMODE><<<grid, ColTma::THREADS, ColTma::smem, st>>>(cp, map, B);
+    return cudaGetLastError();
+}
+
+template <int FLAGS>
+cudaError_t row_launch_tma(const RowParams& rp, int B, cudaStream_t st)
+{
+    static int resident = 0;
+    if (resident == 0) resident = max_ctas(row_pass_tma_kernel<FLAGS>, RowTma::THREADS, RowTma::smem);
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    int per = 0;
+    const int warps = balanced_grid(B * kN, resident * RowTma::WARPS, &per);
+    const int grid = (warps + RowTma::WARPS - 1) / RowTma::WARPS;
+    row_pass_tma_kernel<FLAGS><<<grid, RowTma::THREADS, RowTma::smem, st>>>(rp, B, per);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t tma_attr(K kernel, size_t bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t col_pass_tma_1024(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+{
+    if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr) return cudaErrorNotSupported;
+    switch (hmode * 2 + (conj ? 1 : 0)) {
+    case 0: return col_launch_tma<false, 0>(cp, B, st);
+    case 1: return col_launch_tma<true, 0>(cp, B, st);
+    case 2: return col_launch_tma<false, 1>(cp, B, st);
+    case 3: return col_launch_tma<true, 1>(cp, B, st);
+    case 4: return col_launch_tma<false, 2>(cp, B, st);
+    case 5: return col_launch_tma<true, 2>(cp, B, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t row_pass_tma_1024(int flags, const RowParams& rp, int B, cudaStream_t st)
+{
+    if ((reinterpret_cast<uintptr_t>(rp.field) & 15) != 0 || (reinterpret_cast<uintptr_t>(rp.phasor) & 15) != 0 ||
+        (rp.phi_set_stride & 1) != 0 || rp.err == nullptr || rp.phasor == nullptr)
+        return cudaErrorNotSupported;
+    switch (flags) {
+    case RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE:
+        return row_launch_tma<RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>(rp, B, st);
+    case RP_IN_FREQ | RP_PHASOR | RP_STORE: return row_launch_tma<RP_IN_FREQ | RP_PHASOR | RP_STORE>(rp, B, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t prepare_prop_tma_1024()
+{
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    chk(tma_attr(col_pass_tma_kernel<false, 0>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 0>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 1>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 1>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 2>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 2>, ColTma::smem));
+    chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>, RowTma::smem));
+    chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_STORE>, RowTma::smem));
+    return e;
+}
+
+}  // namespace ts

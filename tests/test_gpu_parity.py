@@ -152,9 +152,9 @@ def test_phasor_screens_give_the_same_fields_as_float_screens():
     assert np.linalg.norm(G1 - G2) / np.linalg.norm(G1) < 1e-6
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_exact_transfer_function_at_1024_both_column_variants(variant, monkeypatch):
-    # dx = 0.1 mm, dz = 2 m at N = 1024: the exact transfer function in both column-pass variants
+    # dx = 0.1 mm, dz = 2 m at N = 1024: the exact transfer function in every column-pass variant
     monkeypatch.setenv("TS_FFT_E", "32")
     monkeypatch.setenv("TS_COL_VARIANT", str(variant))
     N, dx, S = 1024, 1e-4, 2
@@ -350,11 +350,11 @@ def test_large_grid_2048_and_energy():
     assert rel_l2(U[0].cpu().numpy(), ref) < TOL
 
 
-@pytest.mark.parametrize("E,variant", [(16, 0), (32, 0), (32, 1)])
+@pytest.mark.parametrize("E,variant", [(16, 0), (32, 0), (32, 1), (32, 2)])
 def test_both_fft_variants_match_oracle(E, variant, monkeypatch):
     # the autotuner picks 16 or 32 points per thread and, at 32, the column-pass variant (lines shared
-    # by four warps, or one warp per column with the tile staged in shared memory); every candidate
-    # must agree with the oracle, forward and adjoint
+    # by four warps, one warp per column with the tile staged in shared memory, or persistent CTAs with
+    # TMA-prefetched tiles); every candidate must agree with the oracle, forward and adjoint
     monkeypatch.setenv("TS_FFT_E", str(E))
     monkeypatch.setenv("TS_COL_VARIANT", str(variant))
     monkeypatch.setenv("TS_ROW_VARIANT", "0")
@@ -410,6 +410,108 @@ def test_shared_phasor_row_pass_matches_oracle(B, phi_group, monkeypatch):
         assert abs(sums[b, 0].item() / np.sum(np.abs(ref) ** 2) - 1) < 2 * TOL
         back = O.propagate_adjoint(md, [62.5] * S, set_phi, U0[b])
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
+
+
+@pytest.mark.parametrize("B,phi_group", [(4, 2), (8, 8), (3, 3), (1, 1)])
+def test_prefetching_passes_match_oracle(B, phi_group, monkeypatch):
+    # column variant 2 (persistent CTAs, next 8-column tile by TMA) and row variant 2 (persistent warps,
+    # next row and the phasor row by bulk copies), N = 1024, separable transfer function with a tiny
+    # cross term: forward to the field (the last row pass also prefetches), forward to the intensity,
+    # and the adjoint; ragged persistent grids (B = 3, 1)
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    monkeypatch.setenv("TS_PROP_STREAMS", "1")
+    N, dx, S = 1024, 5e-4, 3
+    G = (B + phi_group - 1) // phi_group
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    tune = plan.tuning()
+    assert tune[0] == 32 and tune[5] == 2 and tune[7] == 2
+    phis = np.stack([np.stack([O.make_screen(md, 1e-14, 62.5, 0, 50, s, g) for s in range(S)]) for g in range(G)])
+    ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
+    rng = np.random.default_rng(51)
+    U0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    U = torch.from_numpy(U0).to(DEV)
+    plan.propagate(U, B, phasor=ph, phi_group=phi_group)
+    U2 = torch.from_numpy(U0).to(DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    plan.propagate(U2, B, phasor=ph, phi_group=phi_group, flags=ts.TS_PROP_INTENSITY, intensity=I)
+    g = torch.from_numpy(U0).to(DEV)
+    plan.propagate_backward(g, B, phasor=ph, phi_group=phi_group)
+    plan.device_status()
+    got, Ig, gg = U.cpu().numpy(), I.cpu().numpy(), g.cpu().numpy()
+    for b in range(B):
+        set_phi = np.angle(np.exp(1j * phis[b // phi_group]))
+        ref = O.propagate(md, [62.5] * S, set_phi, U0[b])
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+        assert rel_l2(Ig[b], np.abs(ref) ** 2) < 2 * TOL
+        back = O.propagate_adjoint(md, [62.5] * S, set_phi, U0[b])
+        assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
+
+
+def test_prefetching_column_pass_with_the_series_cross_term(monkeypatch):
+    # dz = 2500 m at dx = 0.5 mm (above the Eq. 7 limit, so the plan allows aliasing): the cross term
+    # reaches 0.015 rad, the separable transfer function applies exp(-i e) as its short series
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    N, dx, S = 1024, 5e-4, 2
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [2500.0] * S, [1e-16] * S, l0=5e-3, L0=10.0, max_batch=1,
+                   flags=ts.TS_PLAN_ALLOW_ALIASING)
+    plan.set_sources([0.05])
+    U = cfield(1, N)
+    plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE, seed=21)
+    g = U.clone()
+    plan.propagate_backward(g, 1, seed=21)
+    plan.device_status()
+    phis = np.stack([O.make_screen(md, 1e-16, 2500.0, 0, 21, s, 0) for s in range(S)])
+    ref = O.propagate(md, [2500.0] * S, phis, O.source_gaussian(N, dx, 0.05))
+    assert rel_l2(U[0].cpu().numpy(), ref) < TOL, rel_l2(U[0].cpu().numpy(), ref)
+    back = O.propagate_adjoint(md, [2500.0] * S, phis, U[0].cpu().numpy())
+    assert rel_l2(g[0].cpu().numpy(), back) < TOL
+
+
+def test_prefetching_pass_wait_runs_out_and_is_reported(monkeypatch):
+    # TS_PLAN_TEST_STALL: the prefetching passes never issue their first copy, so their first bounded
+    # wait runs out (50 ms); the host sees TS_ERR_DEVICE_TIMEOUT and the context stays usable
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    monkeypatch.setenv("TS_PROP_STREAMS", "1")
+    N, dx, S = 1024, 5e-4, 2
+    bad = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=1, flags=ts.TS_PLAN_TEST_STALL)
+    ph = torch.ones((S, N, N), dtype=torch.complex64, device=DEV)
+    U = cfield(1, N)
+    bad.propagate(U, 1, phasor=ph, phi_group=1)
+    with pytest.raises(ts.TsError) as err:
+        bad.device_status()
+    assert err.value.status == 5  # TS_ERR_DEVICE_TIMEOUT
+    bad.device_status()  # cleared
+    good = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=1)
+    good.set_sources([0.01])
+    V = cfield(1, N)
+    good.propagate(V, 1, flags=ts.TS_PROP_SOURCE, seed=5)
+    good.device_status()
+    md = omedium(N, dx)
+    phis = np.stack([O.make_screen(md, 1e-15, 62.5, 0, 5, s, 0) for s in range(S)])
+    ref = O.propagate(md, [62.5] * S, phis, O.source_gaussian(N, dx, 0.01))
+    assert rel_l2(V[0].cpu().numpy(), ref) < TOL
+
+
+def test_tuning_candidate_table():
+    N, dx, S = 1024, 5e-4, 2
+    plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=4)
+    cands = plan.tuning_candidates()
+    assert [(e, cv, rv) for e, cv, rv, _ in cands] == [(16, 0, 0), (32, 0, 0), (32, 1, 0), (32, 0, 1), (32, 2, 0),
+                                                      (32, 0, 2), (32, 2, 2)]
+    t = plan.tuning()
+    chosen = [c for c in cands if (c[0], c[1], c[2]) == (t[0], t[5], t[7])]
+    assert len(chosen) == 1
+    timed = [c[3] for c in cands if c[3] > 0]
+    if timed:  # not a cached result
+        assert chosen[0][3] == min(timed)
 
 
 @pytest.mark.parametrize("groups", [2, 4])
