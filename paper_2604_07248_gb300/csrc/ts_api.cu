@@ -296,9 +296,11 @@ ts_status autotune(Plan& p)
 }
 
 // Second autotuner stage: how many field groups to propagate concurrently (1, 2 or 4 streams), timed
-// as one column + one row pass of B_t workspace fields per candidate.  Cached like the first stage;
+// as runs of four column + row pass pairs of B_t workspace fields per fork (the reported cost is per
+// pair).  Cached like the first stage;
 // TS_PROP_STREAMS=1|2|4 forces a choice.
 std::map<std::tuple<int, int, int, int, int>, int> g_group_cache;
+constexpr int kTuneSteps = 4;  // column + row pass pairs per fork in the group timing
 
 ts_status autotune_groups(Plan& p)
 {
@@ -349,8 +351,11 @@ ts_status autotune_groups(Plan& p)
                 ra.phase_sign = 1.0f;
                 ra.B = bg;
                 ra.b0 = b0;
-                x = launch_col_pass(p, 0, false, ra.field, bg, st);
-                if (x == cudaSuccess) x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, st);
+                // a run of steps per fork, as in ts_propagate: the groups overlap in the steady state
+                for (int s = 0; s < kTuneSteps && x == cudaSuccess; ++s) {
+                    x = launch_col_pass(p, 0, false, ra.field, bg, st);
+                    if (x == cudaSuccess) x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, st);
+                }
             }
             for (int g = 1; g < groups && x == cudaSuccess; ++g) {
                 x = cudaEventRecord(p.join[g - 1], p.aux[g - 1]);
@@ -365,7 +370,7 @@ ts_status autotune_groups(Plan& p)
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        p.tune_group_us[c] = ms * 1000.0f / 5.0f;
+        p.tune_group_us[c] = ms * 1000.0f / (5.0f * kTuneSteps);
         if (e == cudaSuccess && p.tune_group_us[c] < best * 0.97f) {  // prefer fewer streams unless 3 % faster
             best = p.tune_group_us[c];
             best_g = groups;

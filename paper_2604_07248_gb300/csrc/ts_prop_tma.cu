@@ -17,6 +17,8 @@
 // returns after a second bounded wait for its copy in flight.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "ts_device.cuh"
 #include "ts_prop_decl.h"
 
@@ -216,7 +218,7 @@ struct RowTma {
 };
 
 template <int FLAGS>
-__global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const RowParams a, int B, int per_warp)
+__global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const RowParams a, int B)
 {
     using C = RowTma::C;
     static_assert((FLAGS & RP_IN_FREQ) && (FLAGS & RP_PHASOR) && (FLAGS & RP_STORE) && !(FLAGS & RP_INTENSITY) &&
@@ -228,21 +230,20 @@ __global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const 
     float2* line = reinterpret_cast<float2*>(sm + RowTma::off_line) + warp * RowTma::LS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RowTma::off_bar) + warp;
     const int rows = B * kN;
-    // rows gw * per_warp .. + per_warp - 1 of the launch (consecutive rows of one field share phasor sets)
-    const int gw = blockIdx.x * RowTma::WARPS + warp;
-    const int r0 = gw * per_warp, r1 = min(rows, r0 + per_warp);
+    // rows gw, gw + stride, ... of the launch (strided over every warp of the grid)
+    const int gw = blockIdx.x * RowTma::WARPS + warp, stride = gridDim.x * RowTma::WARPS;
     if (lane == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
-        if (r0 < r1 && !a.stall) {
+        if (gw < rows && !a.stall) {
             mbar_expect_tx(bar, RowTma::ROW_BYTES);
-            bulk_load(line, a.field + (size_t)r0 * kN, RowTma::ROW_BYTES, bar);
+            bulk_load(line, a.field + (size_t)gw * kN, RowTma::ROW_BYTES, bar);
         }
     }
     stage_twiddles_c<C>(tw, a.tw);
     __syncthreads();
     uint32_t parity = 0;
-    for (int r = r0; r < r1; ++r) {
+    for (int r = gw; r < rows; r += stride) {
         const int b = r / kN, j = r % kN;
         float2 v[32];
         if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, a.budget))) {
@@ -282,17 +283,17 @@ __global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const 
         __syncwarp();
         if constexpr (FLAGS & RP_OUT_FREQ) {
             fft_stage_c<C, 0, -1>(v, line, lane, tw, WarpBar());
-            if (lane == 0 && r + 1 < r1) {
+            if (lane == 0 && r + stride < rows) {
                 fence_proxy_async();
                 mbar_expect_tx(bar, RowTma::ROW_BYTES);
-                bulk_load(line, a.field + (size_t)(r + 1) * kN, RowTma::ROW_BYTES, bar);
+                bulk_load(line, a.field + (size_t)(r + stride) * kN, RowTma::ROW_BYTES, bar);
             }
             fft_stage_c<C, 1, -1>(v, line, lane, tw, WarpBar());
         } else {
-            if (lane == 0 && r + 1 < r1) {
+            if (lane == 0 && r + stride < rows) {
                 fence_proxy_async();
                 mbar_expect_tx(bar, RowTma::ROW_BYTES);
-                bulk_load(line, a.field + (size_t)(r + 1) * kN, RowTma::ROW_BYTES, bar);
+                bulk_load(line, a.field + (size_t)(r + stride) * kN, RowTma::ROW_BYTES, bar);
             }
         }
         float2* row = a.field + (size_t)r * kN;
@@ -332,14 +333,6 @@ int max_ctas(K kernel, int threads, size_t smem)
     return sms * per;
 }
 
-// a balanced persistent grid: the fewest CTAs that keep every CTA's share of the work units at the
-// share a full-residency grid would need
-inline int balanced_grid(int units, int resident, int* per)
-{
-    const int p = (units + resident - 1) / resident;
-    *per = p;
-    return (units + p - 1) / p;
-}
 
 template <bool CONJ, int HMODE>
 cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
@@ -357,8 +350,9 @@ cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
     static int resident = 0;
     if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE>, ColTma::THREADS, ColTma::smem);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
-    int per = 0;
-    const int grid = balanced_grid(B * ColTma::TPF, resident, &per);
+    // full residency, tiles strided over the CTAs: the two CTAs an SM holds share its issue slots, so
+    // filling every slot keeps each SM's tile count within one of the mean
+    const int grid = std::min(B * ColTma::TPF, resident);
     col_pass_tma_kernel<CONJ, HMODE><<<grid, ColTma::THREADS, ColTma::smem, st>>>(cp, map, B);
     return cudaGetLastError();
 }
@@ -369,10 +363,8 @@ cudaError_t row_launch_tma(const RowParams& rp, int B, cudaStream_t st)
     static int resident = 0;
     if (resident == 0) resident = max_ctas(row_pass_tma_kernel<FLAGS>, RowTma::THREADS, RowTma::smem);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
-    int per = 0;
-    const int warps = balanced_grid(B * kN, resident * RowTma::WARPS, &per);
-    const int grid = (warps + RowTma::WARPS - 1) / RowTma::WARPS;
-    row_pass_tma_kernel<FLAGS><<<grid, RowTma::THREADS, RowTma::smem, st>>>(rp, B, per);
+    const int grid = std::min((B * kN + RowTma::WARPS - 1) / RowTma::WARPS, resident);  // full residency
+    row_pass_tma_kernel<FLAGS><<<grid, RowTma::THREADS, RowTma::smem, st>>>(rp, B);
     return cudaGetLastError();
 }
 
