@@ -124,14 +124,16 @@ def algorithmic_bytes(N, B, S):
     """Bytes one launch of each kernel kind must move (the roofline numerator), per the 2-pass model:
     column pass: field read + write; row passes: field read + write, screen read once (shared by the
     beams), the first pass writes only; screen synthesis: AR state read + write, column-transformed
-    spectrum write + read, screen phasor write (8 B), PSD shape read once."""
+    spectrum write + read, screen phasor write (8 B), PSD shape read once; fused propagation: the
+    whole ts_propagate call (first row pass and S column + row passes, see propagate_bytes)."""
     px = N * N
     col = 16 * B * px
     row_first = 8 * B * px
     row_mid = 16 * B * px + 8 * px
     row_avg = (row_first + S * row_mid) / (S + 1)
     screens = S * 40 * px + 4 * px
-    return {0: col, 1: row_avg, 2: screens}
+    fused = propagate_bytes(N, B, S, B)  # one launch = the whole propagation of the B fields
+    return {0: col, 1: row_avg, 2: screens, 3: fused}
 
 
 def hbm_peak():
@@ -223,7 +225,8 @@ def run_gpu(args):
         return float(tt.item())
 
     groups = plan.tuning()[3]  # concurrent field groups chosen by the autotuner
-    launches_per_step = 2 + groups * (1 + 2 * S)
+    fused = plan.tuning_fused()  # (fused persistent launch chosen, us per-pass, us fused)
+    launches_per_step = 2 + (1 if fused[0] else groups * (1 + 2 * S))
     for _ in range(args.warmup):
         step()
     barrier()
@@ -260,7 +263,7 @@ def run_gpu(args):
         t_next[0] = tt + 1
     barrier()
     plan_for_timing = prof_plan
-    kinds = {0: "col_pass", 1: "row_pass", 2: "screen_synthesis"}
+    kinds = {0: "col_pass", 1: "row_pass", 2: "screen_synthesis", 3: "propagation_fused"}
     kt = {k: plan_for_timing.timing_read(k) for k in kinds}
     plan_for_timing.timing(False)
     algo = algorithmic_bytes(N, B, S)
@@ -390,6 +393,7 @@ def run_gpu(args):
                                         [round(x, 2) if isinstance(x, float) else
                                          ([round(y, 2) for y in x] if isinstance(x, list) else x)
                                          for x in plan.tuning()])),
+                   "fused": {"chosen": fused[0], "us_per_pass": round(fused[1], 2), "us_fused": round(fused[2], 2)},
                    "l2": "working set 320 MiB (AR spectra 128 + screen phasors 128 + fields 64) > 126 MB L2; no flush"},
         "roofline": roof,
         "split_bf16": split,

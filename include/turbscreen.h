@@ -140,6 +140,19 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
 ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
                                     int* row_variant, float* us);
 
+/* The autotuner's last stage (N = 1024, 32 points per thread, FP32 passes): *fused = 1 when
+ * ts_propagate runs the whole path of a call -- first row pass and S x (column pass, row pass) of
+ * Eq. 1 -- as ONE persistent launch.  Its work items are (pass, field, 8-column or 8-row tile); an
+ * item starts once every tile of the previous pass of its own field is done (bounded waits, error
+ * word as in ts_plan_device_status), so one field's row pass runs while another's column pass
+ * drains, and each CTA prefetches its next item's tile by TMA.  It serves calls whose screens are
+ * given as phasors or regenerated from the seed (when the workspace holds all S screens) and that
+ * store the field (no TS_PROP_INTENSITY); other calls use the per-pass launches.  us_per_pass /
+ * us_fused receive the timed cost in microseconds of one propagation of min(max_batch, 8) fields
+ * each way (0 = not timed: other N, a cached result, or TS_FUSED=0|1 in the environment).
+ * Outputs other than `fused` may be NULL.  Host-only. */
+ts_status ts_plan_tuning_fused(ts_plan plan, int* fused, float* us_per_pass, float* us_fused);
+
 /* Aliasing-limited maximum step of Eq. 7 for this medium and grid (reading: kappa_max = pi/dx,
  * Nyquist spacing 2 pi / (N dx)); returns a negative value for invalid input. */
 double ts_max_step(const ts_medium* medium, const ts_grid* grid);
@@ -269,7 +282,8 @@ ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* t
 /* Kernel timing for roofline measurements.  While enabled, the plan records a CUDA event pair on
  * the launching stream around every launch of: kind 0 = propagation column pass, kind 1 =
  * propagation row pass, kind 2 = screen synthesis (column + row pass of one ts_make_screens /
- * ts_evolve_screens / regeneration call).  `capacity` event pairs are created per kind (no device
+ * ts_evolve_screens / regeneration call), kind 3 = fused propagation (one persistent launch that runs
+ * all passes of a ts_propagate call, see ts_plan_tuning_fused).  `capacity` event pairs are created per kind (no device
  * memory); launches beyond it are not timed.  Enabling resets the counters.
  * ts_plan_timing_read waits for the recorded events and returns the number of timed launches of
  * `kind` and their summed device time in milliseconds. */

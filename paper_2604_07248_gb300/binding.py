@@ -66,6 +66,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float),
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_plan_tuning_candidates": (_I, [_P, _I, C.POINTER(C.c_int), _P, _P, _P, _P]),
+    "ts_plan_tuning_fused": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_cn2_hufnagel_valley": (_I, [_P, _I, _D, _D, _P]),
     "ts_adam_step": (_I, [_P, _P, _P, _P, C.c_longlong, _D, _D, _D, _D, _I, _P]),
@@ -278,6 +279,12 @@ class Plan:
                "ts_plan_tuning_candidates")
         return [(e[i], cv[i], rv[i], us[i]) for i in range(n.value)]
 
+    def tuning_fused(self):
+        """(fused, us per propagation with per-pass launches, us with the fused persistent launch)."""
+        f, a, b = C.c_int(), C.c_float(), C.c_float()
+        _check(load().ts_plan_tuning_fused(self._h, C.byref(f), C.byref(a), C.byref(b)), "ts_plan_tuning_fused")
+        return bool(f.value), a.value, b.value
+
     def set_loss_scale(self, scale: float):
         """Factor on the D2NN receiver loss and its gradients (see ts_plan_set_loss_scale)."""
         _check(load().ts_plan_set_loss_scale(self._h, float(scale)), "ts_plan_set_loss_scale")
@@ -300,7 +307,8 @@ class Plan:
             pass
 
     def timing(self, enable: bool, capacity: int = 0):
-        """Record CUDA events around each launch (kinds: 0 column pass, 1 row pass, 2 screens)."""
+        """Record CUDA events around each launch (kinds: 0 column pass, 1 row pass, 2 screens, 3 fused
+        propagation)."""
         _check(load().ts_plan_timing(self._h, 1 if enable else 0, int(capacity)), "ts_plan_timing")
 
     def timing_read(self, kind: int):

@@ -12,6 +12,7 @@
 #include <tuple>
 
 #include "ts_internal.h"
+#include "ts_prop_decl.h"
 
 namespace ts {
 
@@ -91,7 +92,7 @@ void free_plan(Plan* p)
     if (p->fork) cudaEventDestroy(p->fork);
     void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
                     p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows,
-                    p->tw16 != p->tw ? p->tw16 : nullptr, p->d_err};
+                    p->tw16 != p->tw ? p->tw16 : nullptr, p->d_err, p->ht_all, p->fused_ctr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -136,6 +137,48 @@ ts_status prop_range(Plan& p, float2* U, int b0, int B, const float* phi, const 
     ra.phase_sign = 1.0f;
     ra.B = B;
     ra.b0 = b0;
+    const bool aligned = (reinterpret_cast<uintptr_t>(U) & 15) == 0 && (reinterpret_cast<uintptr_t>(phasor) & 15) == 0;
+    if (p.fused && aligned && !(flags & TS_PROP_INTENSITY) && (phasor || (!phi && p.regen_all))) {
+        // the whole path in one persistent launch
+        const uint32_t rb = real_base + (uint32_t)(b0 / phi_group);
+        FusedParams fp{};
+        fp.field = Ur;
+        fp.tw = p.tw;
+        fp.ht = p.ht_all;
+        if (phasor) {
+            fp.phasor = reinterpret_cast<const float2*>(phasor) + set0;
+            fp.phi_off = b0 % phi_group;
+        } else {
+            ts_status sr = regen_screen(p, seed, rb, G, -1, st);
+            if (sr != TS_OK) return sr;
+            fp.phasor = p.ws_phi;
+            fp.phi_off = b0 % phi_group;
+        }
+        fp.set_stride = (long long)S * N2;
+        fp.phi_group = phi_group;
+        fp.phase_sign = 1.0f;
+        fp.S = S;
+        fp.B = B;
+        fp.source = (flags & TS_PROP_SOURCE) ? 1 : 0;
+        fp.src_off = b0;
+        fp.n_src = p.n_src > 0 ? p.n_src : 1;
+        fp.done = p.fused_ctr;
+        fp.err = p.d_err;
+        fp.budget = p.tc_budget;
+        fp.stall = p.test_stall ? 1 : 0;
+        fp.inv_k2 = (float)(1.0 / (p.k * p.k));
+        for (int s = 0; s < S; ++s) {
+            fp.ccross[s] = (float)(p.dz[s] / (4.0 * p.k * p.k * p.k));
+            fp.dcoef[s] = (float)(p.dz[s] / (2.0 * p.k * p.k * p.k));
+        }
+        for (int i = 0; i < kMaxSources; ++i) fp.src_coef[i] = i < p.n_src ? p.src_coef[i] : -1.0f;
+        const int hmode = p.sep_transfer ? (p.tiny_cross ? 2 : 1) : 0;
+        cudaError_t e = cudaErrorNotSupported;
+        ts_status sf = cuda_check(timed(p, 3, st, [&] { return e = prop_fused_1024(hmode, fp, st); }),
+                                  "ts_propagate fused launch");
+        if (e != cudaErrorNotSupported) return sf;
+        set_error("");  // arguments the fused launch does not take: per-pass launches below
+    }
     const int f0 = ((flags & TS_PROP_SOURCE) ? RP_IN_SOURCE : 0) | RP_OUT_FREQ | RP_STORE;
     ts_status stt =
         cuda_check(timed(p, 1, st, [&] { return launch_row_pass(p, f0, ra, st); }), "ts_propagate first row pass");
@@ -183,6 +226,34 @@ ts_status prop_range(Plan& p, float2* U, int b0, int B, const float* phi, const 
         if (stt != TS_OK) return stt;
     }
     return TS_OK;
+}
+
+// Eq. 1 for the whole batch.  With the screens given, the fields split into groups propagated
+// concurrently on the plan's extra streams (fork / join through events, so the call stays asynchronous
+// and capturable): one group's partial last waves overlap another's kernels.  Regenerated screens share
+// one workspace, and the fused persistent launch fills the GPU by itself: no split.
+ts_status propagate_groups(Plan& p, float2* U, int B, const float* phi, const void* phasor, int phi_group, int flags,
+                           uint64_t seed, uint32_t real_base, float* intensity, double* rows, cudaStream_t st)
+{
+    const bool fused_call = p.fused && !(flags & TS_PROP_INTENSITY);
+    const int groups = ((phi || phasor) && !fused_call) ? std::min(p.prop_groups, B) : 1;
+    ts_status stt = TS_OK;
+    if (groups <= 1) return prop_range(p, U, 0, B, phi, phasor, phi_group, flags, seed, real_base, intensity, rows, st);
+    stt = cuda_check(cudaEventRecord(p.fork, st), "ts_propagate fork");
+    for (int g = 1; g < groups && stt == TS_OK; ++g)
+        stt = cuda_check(cudaStreamWaitEvent(p.aux[g - 1], p.fork, 0), "ts_propagate fork");
+    const int per = (B + groups - 1) / groups;
+    for (int g = 0; g < groups && stt == TS_OK; ++g) {
+        const int b0 = g * per, bg = std::min(per, B - b0);
+        if (bg <= 0) break;
+        stt = prop_range(p, U, b0, bg, phi, phasor, phi_group, flags, seed, real_base, intensity, rows,
+                         g == 0 ? st : p.aux[g - 1]);
+    }
+    for (int g = 1; g < groups && stt == TS_OK; ++g) {
+        stt = cuda_check(cudaEventRecord(p.join[g - 1], p.aux[g - 1]), "ts_propagate join");
+        if (stt == TS_OK) stt = cuda_check(cudaStreamWaitEvent(st, p.join[g - 1], 0), "ts_propagate join");
+    }
+    return stt;
 }
 
 // Autotuner: for N >= 512 the propagation passes exist with E = 16 and E = 32 points per thread
@@ -385,6 +456,72 @@ ts_status autotune_groups(Plan& p)
     return TS_OK;
 }
 
+// Third autotuner stage (N = 1024, 32 points per thread, FP32 passes): one propagation of B_t
+// workspace fields through the plan's S steps, by per-pass launches (the variants and field groups
+// chosen above) or as one fused persistent launch; the fused launch is kept when it is faster.
+// Cached like the other stages; TS_FUSED=0|1 forces a choice.
+std::map<std::tuple<int, int, int, int, int, int>, int> g_fused_cache;
+
+ts_status autotune_fused(Plan& p)
+{
+    p.fused = false;
+    if (p.N != 1024 || p.fft_e != 32 || p.split_bf16 || !p.ht_all || !p.fused_ctr) return TS_OK;
+    if (const char* env = std::getenv("TS_FUSED")) {
+        p.fused = std::atoi(env) != 0;
+        return TS_OK;
+    }
+    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
+    const size_t N2 = (size_t)p.N * p.N;
+    const auto key = std::make_tuple(p.device, p.N, Bt, p.S, (p.sep_transfer ? 1 : 0) + (p.tiny_cross ? 2 : 0),
+                                     p.col_variant + 8 * p.row_variant + 64 * p.prop_groups);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_fused_cache.find(key);
+        if (it != g_fused_cache.end()) {
+            p.fused = it->second != 0;
+            return TS_OK;
+        }
+    }
+    // fields in ws_phi (>= max_batch N^2), the S phasor screens of one set in ws_y (>= S N^2)
+    float2* U = p.ws_phi;
+    const float2* ph = p.ws_y;
+    cudaError_t e = cudaMemset(p.ws_y, 0, sizeof(float2) * N2 * p.S);
+    if (e == cudaSuccess) e = cudaMemset(p.ws_phi, 0, sizeof(float2) * N2 * Bt);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (fused)");
+    ts_status stt = TS_OK;
+    for (int c = 0; c < 2 && stt == TS_OK; ++c) {
+        p.fused = c == 1;
+        auto once = [&]() { return propagate_groups(p, U, Bt, nullptr, ph, Bt, 0, 0, 0, nullptr, nullptr, nullptr); };
+        for (int w = 0; w < 2 && stt == TS_OK; ++w) stt = once();
+        if (stt == TS_OK) stt = cuda_check(cudaEventRecord(e0, nullptr), "autotune (fused)");
+        for (int r = 0; r < 5 && stt == TS_OK; ++r) stt = once();
+        if (stt == TS_OK) stt = cuda_check(cudaEventRecord(e1, nullptr), "autotune (fused)");
+        if (stt == TS_OK) stt = cuda_check(cudaEventSynchronize(e1), "autotune (fused)");
+        float ms = 0.0f;
+        if (stt == TS_OK) stt = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "autotune (fused)");
+        p.tune_fused_us[c] = ms * 1000.0f / 5.0f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (stt != TS_OK) {
+        p.fused = false;
+        return stt;
+    }
+    {
+        int code = 0;  // a fused launch whose bounded waits ran out is never chosen
+        cudaError_t x = cudaMemcpy(&code, p.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (x == cudaSuccess && code != 0) x = cudaMemset(p.d_err, 0, sizeof(int));
+        if (x != cudaSuccess) return cuda_check(x, "ts_plan_create autotune (fused)");
+        p.fused = code == 0 && p.tune_fused_us[1] < p.tune_fused_us[0];
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_fused_cache[key] = p.fused ? 1 : 0;
+    return TS_OK;
+}
+
 }  // namespace
 }  // namespace ts
 
@@ -513,6 +650,10 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     p->regen_all = (size_t)max_batch * S * N2 * sizeof(float2) <= (256ull << 20);
     ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * (p->regen_all ? S : 1) * N2));
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
+    if (N == 1024 && !p->split_bf16) {
+        ok(dalloc(*p, &p->ht_all, (size_t)S * N));
+        ok(dalloc(*p, &p->fused_ctr, (size_t)(2 * S + 1) * max_batch + 1));
+    }
     // device error word and wait budget of the passes with bounded waits (tensor-core and prefetching passes)
     ok(dalloc(*p, &p->d_err, 1));
     if (p->d_err) ok(cudaMemset(p->d_err, 0, sizeof(int)));
@@ -552,6 +693,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         ok(cudaMemcpy(p->shb, shb, sizeof(double) * S * kShCoef, cudaMemcpyHostToDevice));
     }
     ok(build_tables(*p));
+    if (p->ht_all) ok(build_ht_table(p->ht_all, p->P, S, p->dk, nullptr));
     ok(prepare_prop_kernels(N));
     if (p->split_bf16) ok(prepare_tc_prop());
     ok(prepare_screen_kernels(N));
@@ -574,6 +716,7 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
     {
         ts_status st = autotune(*p);
         if (st == TS_OK) st = autotune_groups(*p);
+        if (st == TS_OK) st = autotune_fused(*p);
         if (st != TS_OK) {
             free_plan(p);
             return st;
@@ -625,6 +768,16 @@ ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_p
         if (row_variant) row_variant[c] = kCandRow[c];
         if (us) us[c] = p->tune_us[c];
     }
+    return TS_OK;
+}
+
+ts_status ts_plan_tuning_fused(ts_plan plan, int* fused, float* us_per_pass, float* us_fused)
+{
+    if (!plan || !fused) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning_fused: need plan and output");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    *fused = p->fused ? 1 : 0;
+    if (us_per_pass) *us_per_pass = p->tune_fused_us[0];
+    if (us_fused) *us_fused = p->tune_fused_us[1];
     return TS_OK;
 }
 
@@ -742,30 +895,8 @@ ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, const
         return fail(TS_ERR_INVALID_ARG, "ts_propagate: TS_PROP_NO_FIELD needs TS_PROP_INTENSITY");
     cudaStream_t st = as_stream(stream);
     float2* U = reinterpret_cast<float2*>(field);
-    // With the screens given, the fields split into groups propagated concurrently on the plan's extra
-    // streams (fork / join through events, so the call stays asynchronous and capturable): one group's
-    // partial last waves overlap another's kernels.  Regenerated screens share one workspace: no split.
-    const int groups = (phi || phasor) ? std::min(p->prop_groups, B) : 1;
-    ts_status stt = TS_OK;
-    if (groups <= 1) {
-        stt = prop_range(*p, U, 0, B, phi, phasor, phi_group, flags, seed, real_base, intensity,
-                         beam_sums ? p->ws_rows : nullptr, st);
-    } else {
-        stt = cuda_check(cudaEventRecord(p->fork, st), "ts_propagate fork");
-        for (int g = 1; g < groups && stt == TS_OK; ++g)
-            stt = cuda_check(cudaStreamWaitEvent(p->aux[g - 1], p->fork, 0), "ts_propagate fork");
-        const int per = (B + groups - 1) / groups;
-        for (int g = 0; g < groups && stt == TS_OK; ++g) {
-            const int b0 = g * per, bg = std::min(per, B - b0);
-            if (bg <= 0) break;
-            stt = prop_range(*p, U, b0, bg, phi, phasor, phi_group, flags, seed, real_base, intensity,
-                             beam_sums ? p->ws_rows : nullptr, g == 0 ? st : p->aux[g - 1]);
-        }
-        for (int g = 1; g < groups && stt == TS_OK; ++g) {
-            stt = cuda_check(cudaEventRecord(p->join[g - 1], p->aux[g - 1]), "ts_propagate join");
-            if (stt == TS_OK) stt = cuda_check(cudaStreamWaitEvent(st, p->join[g - 1], 0), "ts_propagate join");
-        }
-    }
+    ts_status stt = propagate_groups(*p, U, B, phi, phasor, phi_group, flags, seed, real_base, intensity,
+                                     beam_sums ? p->ws_rows : nullptr, st);
     if (stt != TS_OK) return stt;
     if (beam_sums) return cuda_check(launch_row_sums(*p, p->ws_rows, B, beam_sums, st), "ts_propagate beam sums");
     return TS_OK;
@@ -878,7 +1009,7 @@ ts_status ts_plan_timing(ts_plan plan, int enable, int capacity)
 
 ts_status ts_plan_timing_read(ts_plan plan, int kind, int* launches, double* total_ms)
 {
-    if (!plan || kind < 0 || kind > 2 || !launches || !total_ms)
+    if (!plan || kind < 0 || kind > 3 || !launches || !total_ms)
         return fail(TS_ERR_INVALID_ARG, "ts_plan_timing_read: bad arguments");
     Plan* p = reinterpret_cast<Plan*>(plan);
     double tot = 0.0;

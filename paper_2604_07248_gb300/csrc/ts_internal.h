@@ -51,6 +51,10 @@ struct Plan {
                                // 2 = persistent warps with bulk-copy prefetch of rows and phasor rows
     float tune_us[8] = {};     // autotuner timings of one column + row pass per candidate (kCandE/Col/Row)
     int prop_groups = 1;       // field groups propagated concurrently on separate streams (1, 2 or 4)
+    bool fused = false;        // ts_propagate runs the whole path as one persistent launch (N = 1024, E = 32)
+    float tune_fused_us[2] = {0, 0};  // autotuner: one propagation through per-pass launches / fused launch
+    float4* ht_all = nullptr;  // [S][N] (P_s, ky^2) for the fused launch (N = 1024)
+    int* fused_ctr = nullptr;  // [(2S+1) max_batch + 1] completion counters and work counter of the fused launch
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
@@ -77,10 +81,11 @@ struct Plan {
     double* ws_rows = nullptr;    // [max_batch][N][2] per-row beam sums
     size_t bytes = 0;
 
-    // optional per-kernel-kind event timing (kinds: 0 column pass, 1 row pass, 2 screen synthesis)
+    // optional per-kernel-kind event timing (kinds: 0 column pass, 1 row pass, 2 screen synthesis,
+    // 3 fused propagation)
     bool timing = false;
-    std::vector<cudaEvent_t> ev[3];
-    int ev_used[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev[4];
+    int ev_used[4] = {0, 0, 0, 0};
 };
 
 // error plumbing

@@ -92,6 +92,7 @@ cudaError_t prepare_prop_kernels(int N)
 {
     if (N == 1024) {
         cudaError_t e = prepare_prop_tma_1024();
+        if (e == cudaSuccess) e = prepare_prop_fused_1024();
         if (e != cudaSuccess) return e;
     }
     switch (N) {

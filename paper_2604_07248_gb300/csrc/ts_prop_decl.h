@@ -54,6 +54,36 @@ cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams&
 template <int N>
 cudaError_t prepare_prop_n();
 
+// The whole propagation of B fields of N = 1024 (first row pass, S column + row passes) in one
+// persistent launch (ts_prop_fused.cu).  Field b (0-based in this launch) uses screen set
+// (b + phi_off) / phi_group, whose screen s is the phasor row block phasor + s N^2 + set * set_stride.
+struct FusedParams {
+    float2* field;           // [B][N][N] complex64, in place
+    const float2* tw;        // Stockham stage twiddles (32 points per thread)
+    const float4* ht;        // [S][N] (P_s(m), ky(m)^2): the separable factor of H_s and ky^2
+    const float2* phasor;    // exp(i phi): screen s of set g at phasor + s N^2 + g set_stride
+    long long set_stride;
+    int phi_group, phi_off;
+    float phase_sign;
+    int S, B;
+    int source;              // phase 0 generates the sources instead of reading the field
+    int src_off, n_src;      // field b starts as source (b + src_off) mod n_src
+    int* done;               // [(2S+1) B + 1] completed tiles per (phase, field), then the work counter
+    int* head;               // set by the launcher
+    int* err;
+    long long budget;
+    int stall;               // test hook: no input copy is issued, so the first input wait runs out
+    float inv_k2;
+    float ccross[kMaxScreens];
+    float dcoef[kMaxScreens];
+    float src_coef[kMaxSources];
+};
+// cudaErrorNotSupported when the arguments do not fit the fused launch (alignment, sizes)
+cudaError_t prop_fused_1024(int hmode, const FusedParams& fp, cudaStream_t st);
+cudaError_t prepare_prop_fused_1024();
+// ht[s][m] = (P[s][m], (dk kidx(m))^2) for N = 1024
+cudaError_t build_ht_table(float4* ht, const float2* P, int S, double dk, cudaStream_t st);
+
 // the TMA-prefetching passes (ts_prop_tma.cu); cudaErrorNotSupported when the arguments do not fit them
 cudaError_t col_pass_tma_1024(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
 cudaError_t row_pass_tma_1024(int flags, const RowParams& rp, int B, cudaStream_t st);

@@ -1,0 +1,367 @@
+// ts_prop_fused.cu -- the whole Eq. 1 propagation of a batch of N = 1024 fields (first row pass, then
+// S x (column pass, row pass)) as ONE persistent launch.
+//
+// Work items are (phase, field, tile) in phase-major order: phase 0 = first row pass (source or
+// field -> row FFT), phase 2s+1 = column pass of step s (column FFT, x H_s, column IFFT), phase 2s+2 =
+// row pass of step s (row IFFT, x exp(i phi_s), row FFT unless s = S-1).  A tile is 8 columns (column
+// phases) or 8 rows (row phases) of one field: 128 tiles per field and phase.  CTAs take items from a
+// global counter; an item of phase p > 0 needs all 128 tiles of phase p-1 of its own field, and
+// since items are handed out in order, every tile it waits for was taken earlier by a running CTA:
+// the launch cannot deadlock for any grid size.  While one field's column pass drains, other
+// fields' row passes already run, so no per-pass launch tail idles the GPU.
+//
+// Each CTA takes its next item when it starts the current one, and issues the next item's input
+// copies (a 64 KiB column tile by four 2-D TMA boxes plus the step's 16 KiB (P, ky^2) table, or eight
+// 8 KiB field rows by bulk copies) as soon as the current item's last shared-memory exchange has been
+// read and the next item's dependency is already met; otherwise it waits for the dependency (bounded)
+// when it gets there.  Row tiles fetch their screen phasor rows with per-warp bulk copies under the
+// second stage of the inverse FFT.
+//
+// Completion: a tile's stores, a block barrier, then thread 0 fences and adds 1 to the (phase, field)
+// counter; consumers acquire-load the counter and fence the async proxy before their copies read the
+// data.  Every wait (dependency, copy) is bounded by the plan's clock64 budget; one that runs out
+// sets the error word (read by ts_plan_device_status), after which every CTA stops at its next item.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "ts_async.cuh"
+#include "ts_device.cuh"
+#include "ts_prop_decl.h"
+
+namespace ts {
+namespace {
+
+using namespace async;
+constexpr int kN = 1024;
+constexpr int kErrDepWait = 5;  // error word: a dependency or copy wait of the fused launch ran out
+
+struct Fused {
+    using C = FftCfg<kN, 32>;
+    static constexpr int THREADS = 256, WARPS = 8, W = 8, TPF = kN / W;
+    static constexpr int LSC = C::padded + 2;  // column stride of the column-tile exchange
+    static constexpr int LSR = C::padded;      // line stride of the row-tile lines
+    static constexpr int TILE_BYTES = W * kN * 8;
+    static constexpr int HT_BYTES = kN * 16;
+    static constexpr size_t off_ht = sizeof(float2) * C::tw_smem;
+    static constexpr size_t off_buf = off_ht + HT_BYTES;
+    static constexpr size_t off_bar = off_buf + sizeof(float2) * W * LSC;
+    static constexpr size_t off_int = off_bar + 8 * (1 + WARPS);
+    static constexpr size_t smem = off_int + 16;
+    static_assert(W * LSC >= W * kN && W * LSC >= WARPS * LSR, "tile, lines and exchanges fit the buffer");
+    static_assert(off_buf % 128 == 0 && off_ht % 128 == 0 && (LSR * 8) % 16 == 0, "copy alignment");
+};
+
+__device__ __forceinline__ void item_decode(int it, int per_phase, int& p, int& b, int& tile)
+{
+    p = it / per_phase;
+    const int rem = it - p * per_phase;
+    b = rem / Fused::TPF;
+    tile = rem - b * Fused::TPF;
+}
+
+// thread 0: the input copies of item `it` (phase p, field b, tile) on the CTA's input barrier
+__device__ __forceinline__ void issue_input(const FusedParams& a, const CUtensorMap* map, int p, int b, int tile,
+                                            float2* buf, float4* ht, uint64_t* bin)
+{
+    if (p & 1) {  // column tile + the step's transfer table
+        const int s = (p - 1) >> 1;
+        mbar_expect_tx(bin, Fused::TILE_BYTES + Fused::HT_BYTES);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tma_load_2d(buf + q * 256 * Fused::W, map, 16 * tile, b * kN + q * 256, bin);
+        bulk_load(ht, a.ht + (size_t)s * kN, Fused::HT_BYTES, bin);
+    } else {  // 8 field rows, one per warp line
+        mbar_expect_tx(bin, Fused::TILE_BYTES);
+        const float2* src = a.field + ((size_t)b * kN + (size_t)tile * Fused::WARPS) * kN;
+#pragma unroll
+        for (int w = 0; w < Fused::WARPS; ++w) bulk_load(buf + w * Fused::LSR, src + (size_t)w * kN, kN * 8, bin);
+    }
+}
+
+template <int HMODE>
+__global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const FusedParams a,
+                                                                       const __grid_constant__ CUtensorMap tmap)
+{
+    using C = Fused::C;
+    extern __shared__ __align__(128) unsigned char sm[];
+    float2* tw = reinterpret_cast<float2*>(sm);
+    float4* ht = reinterpret_cast<float4*>(sm + Fused::off_ht);
+    float2* buf = reinterpret_cast<float2*>(sm + Fused::off_buf);
+    uint64_t* bin = reinterpret_cast<uint64_t*>(sm + Fused::off_bar);
+    uint64_t* bph = bin + 1;
+    int* s_int = reinterpret_cast<int*>(sm + Fused::off_int);  // [0] first item, [1] next item
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int per_phase = a.B * Fused::TPF;
+    const int total = (2 * a.S + 1) * per_phase;
+    int issued_for = -1;  // thread 0: the item whose input copies are in flight or have landed
+
+    if (tid == 0) {
+        mbar_init(bin, 1);
+        for (int w = 0; w < Fused::WARPS; ++w) mbar_init(bph + w, 1);
+        mbar_init_fence();
+        s_int[0] = atomicAdd(a.head, 1);
+    }
+    stage_twiddles_c<C>(tw, a.tw);
+    __syncthreads();
+    int cur = s_int[0];
+    uint32_t pin = 0, pph = 0;
+
+    // thread 0: input of `nxt` if its dependency is met now (no wait); returns whether issued
+    auto try_prefetch = [&](int nxt) {
+        if (nxt >= total || a.stall) return;
+        int p, b, tile;
+        item_decode(nxt, per_phase, p, b, tile);
+        if (p == 0 && a.source) return;
+        if (p > 0 && ld_acquire(a.done + (p - 1) * a.B + b) < Fused::TPF) return;
+        fence_proxy_async_global();
+        fence_proxy_async();
+        issue_input(a, &tmap, p, b, tile, buf, ht, bin);
+        issued_for = nxt;
+    };
+
+    while (cur < total) {
+        int p, b, tile;
+        item_decode(cur, per_phase, p, b, tile);
+        const bool needs_input = p > 0 || !a.source;
+        int abort_local = 0;
+        if (tid == 0) {
+            s_int[1] = atomicAdd(a.head, 1);
+            if (ld_relaxed(a.err) != 0) {
+                abort_local = 1;  // another CTA gave up: stop
+            } else if (needs_input && issued_for != cur) {
+                bool ok = true;
+                if (p > 0) {
+                    const int* ctr = a.done + (p - 1) * a.B + b;
+                    const long long t0 = clock64();
+                    while (ld_acquire(ctr) < Fused::TPF) {
+                        if (ld_relaxed(a.err) != 0 || clock64() - t0 > a.budget) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                if (ok && !a.stall) {
+                    fence_proxy_async_global();
+                    issue_input(a, &tmap, p, b, tile, buf, ht, bin);
+                    issued_for = cur;
+                }
+                if (!ok) {
+                    atomicExch(a.err, kErrDepWait);
+                    abort_local = 1;
+                }
+            }
+        }
+        if (__syncthreads_or(abort_local)) {
+            if (tid == 0 && issued_for == cur) mbar_wait(bin, pin, a.budget);  // a prefetched copy in flight
+            return;
+        }
+        const int nxt = s_int[1];
+        bool ok = true;
+        if (needs_input) {
+            ok = mbar_wait(bin, pin, a.budget);
+            pin ^= 1u;
+        }
+        bool bad = false;  // this thread's warp saw a phasor-copy wait run out
+        float2 v[32];
+        if (p & 1) {
+            // ---------------- column tile: FFT -> H_s -> IFFT over 8 columns ----------------
+            const int c = tid % Fused::W, t = tid / Fused::W, s = (p - 1) >> 1;
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = buf[(t + 32 * i) * Fused::W + c];
+            }
+            if (__syncthreads_or(!ok)) {  // also: every thread has read the tile before the exchange
+                if (tid == 0) {
+                    atomicExch(a.err, kErrDepWait);
+                    mbar_wait(bin, pin ^ 1u, a.budget);  // the copy in flight, bounded again
+                }
+                return;
+            }
+            float2* line = buf + c * Fused::LSC;
+            const int col = tile * Fused::W + c;
+            fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
+            fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
+            transfer_tile<false, HMODE>(v, ht, col, t, a.ccross[s], a.dcoef[s], a.inv_k2);
+            fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
+            if (tid == 0) try_prefetch(nxt);
+            fft_stage_c<C, 1, +1>(v, line, t, tw, BlockBar());
+            float2* base = a.field + (size_t)b * kN * kN + col;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) base[(size_t)(t + 32 * i) * kN] = v[i];
+        } else {
+            // ---------------- row tile: one row per warp ----------------
+            float2* line = buf + warp * Fused::LSR;
+            const int j = tile * Fused::WARPS + warp;
+            float2* row = a.field + ((size_t)b * kN + j) * kN;
+            if (p == 0 && a.source) {
+                const float coef = a.src_coef[(b + a.src_off) % a.n_src];
+                const float y = (float)(j - kN / 2);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float x = (float)(lane + 32 * i - kN / 2);
+                    v[i] = coef < 0.0f ? make_float2(1.0f, 0.0f) : make_float2(expf(-(x * x + y * y) * coef), 0.0f);
+                }
+            } else {
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) {
+                        atomicExch(a.err, kErrDepWait);
+                        mbar_wait(bin, pin ^ 1u, a.budget);
+                    }
+                    return;
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = line[lane + 32 * i];
+                __syncwarp();
+            }
+            if (p > 0) {
+                const int s = (p >> 1) - 1;
+                fft_stage_c<C, 0, +1>(v, line, lane, tw, WarpBar());
+                if (lane == 0) {  // the line is free: the screen phasor row comes in under the next stage
+                    const int set = (b + a.phi_off) / a.phi_group;
+                    fence_proxy_async();
+                    mbar_expect_tx(bph + warp, kN * 8);
+                    bulk_load(line, a.phasor + (long long)s * kN * kN + (long long)set * a.set_stride + (size_t)j * kN,
+                              kN * 8, bph + warp);
+                }
+                fft_stage_c<C, 1, +1>(v, line, lane, tw, WarpBar());
+                const bool okp = __all_sync(0xffffffffu, mbar_wait(bph + warp, pph, a.budget));
+                pph ^= 1u;
+                if (!okp) {
+                    bad = true;
+                    if (lane == 0) mbar_wait(bph + warp, pph ^ 1u, a.budget);
+                }
+                if (a.phase_sign > 0.0f) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = cmul(v[i], line[lane + 32 * i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = cmulc(v[i], line[lane + 32 * i]);
+                }
+                __syncwarp();
+            }
+            const bool out_freq = p < 2 * a.S;
+            if (out_freq) fft_stage_c<C, 0, -1>(v, line, lane, tw, WarpBar());
+            __syncthreads();  // every line is free
+            if (tid == 0) try_prefetch(nxt);
+            if (out_freq) fft_stage_c<C, 1, -1>(v, line, lane, tw, WarpBar());
+#pragma unroll
+            for (int i = 0; i < 32; ++i) row[lane + 32 * i] = v[i];
+        }
+        // completion of the tile: visible to the consumers of (phase p, field b)
+        const int ab = __syncthreads_or(bad);
+        if (tid == 0) {
+            if (ab) {
+                atomicExch(a.err, kErrDepWait);
+                if (issued_for == nxt) mbar_wait(bin, pin, a.budget);  // the prefetched copy in flight
+            } else {
+                __threadfence();
+                atomicAdd(a.done + p * a.B + b, 1);
+            }
+        }
+        if (ab) return;
+        cur = nxt;
+    }
+}
+
+__global__ void ht_table_kernel(float4* ht, const float2* P, int S, float dk)
+{
+    const int n = S * kN;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int m = i % kN;
+        const float k = dk * (float)kidx(m, kN);
+        const float2 q = P[i];
+        ht[i] = make_float4(q.x, q.y, k * k, 0.0f);
+    }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    return fn;
+}
+
+template <int HMODE>
+cudaError_t fused_launch(const FusedParams& fp, const CUtensorMap& map, cudaStream_t st)
+{
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prop_fused_kernel<HMODE>, Fused::THREADS, Fused::smem);
+        if (e != cudaSuccess) return e;
+        resident = sms * per;
+    }
+    if (resident <= 0) return cudaErrorInvalidConfiguration;
+    const int items = (2 * fp.S + 1) * fp.B * Fused::TPF;
+    const int grid = std::min(items, resident);
+    prop_fused_kernel<HMODE><<<grid, Fused::THREADS, Fused::smem, st>>>(fp, map);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t build_ht_table(float4* ht, const float2* P, int S, double dk, cudaStream_t st)
+{
+    ht_table_kernel<<<64, 256, 0, st>>>(ht, P, S, (float)dk);
+    return cudaGetLastError();
+}
+
+cudaError_t prop_fused_1024(int hmode, const FusedParams& fp, cudaStream_t st)
+{
+    if ((reinterpret_cast<uintptr_t>(fp.field) & 15) != 0 || (reinterpret_cast<uintptr_t>(fp.phasor) & 15) != 0 ||
+        (fp.set_stride & 1) != 0 || fp.err == nullptr || fp.done == nullptr || fp.B < 1 ||
+        fp.S < 1 || fp.S > kMaxScreens || fp.n_src < 1)
+        return cudaErrorNotSupported;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * kN, (cuuint64_t)fp.B * kN};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * kN * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * Fused::W), 256u};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, fp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    FusedParams f = fp;
+    f.head = fp.done + (2 * fp.S + 1) * fp.B;  // the work counter follows the completion counters
+    cudaError_t e = cudaMemsetAsync(f.done, 0, sizeof(int) * ((2 * f.S + 1) * f.B + 1), st);
+    if (e != cudaSuccess) return e;
+    switch (hmode) {
+    case 0: return fused_launch<0>(f, map, st);
+    case 1: return fused_launch<1>(f, map, st);
+    case 2: return fused_launch<2>(f, map, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_prop_fused_1024()
+{
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    auto attr = [&](auto kernel) {
+        chk(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fused::smem));
+        chk(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    };
+    attr(prop_fused_kernel<0>);
+    attr(prop_fused_kernel<1>);
+    attr(prop_fused_kernel<2>);
+    return e;
+}
+
+}  // namespace ts

@@ -19,65 +19,16 @@
 
 #include <algorithm>
 
+#include "ts_async.cuh"
 #include "ts_device.cuh"
 #include "ts_prop_decl.h"
 
 namespace ts {
 namespace {
 
+using namespace async;
 constexpr int kN = 1024;
 constexpr int kErrTmaWait = 4;  // error word value: a prefetch wait ran out of its budget
-
-__device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(m)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* m, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(s32(m)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, long long budget)
-{
-    if (mbar_try(m, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try(m, parity)) {
-        if (clock64() - t0 > budget) return false;
-    }
-    return true;
-}
-// generic-proxy accesses of this thread (and those ordered before it by a barrier) before later
-// asynchronous-proxy accesses of shared memory
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 2-D tiled tensor copy global -> shared, completion counted in bytes on the mbarrier
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* m)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            s32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(s32(m))
-        : "memory");
-}
-// contiguous bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s32(dst)),
-                 "l"(src), "r"(bytes), "r"(s32(m))
-                 : "memory");
-}
 
 // ---------------------------------------------------------------------------------------------
 // column pass
@@ -95,47 +46,6 @@ struct ColTma {
     static_assert(W * LS >= W * kN, "the dense tile fits the exchange buffer");
     static_assert(off_buf % 128 == 0, "TMA destination alignment");
 };
-
-// v[i] (frequency m = t + 32 i of column col) *= H or conj(H).  ht[m] = (P(m), ky(m)^2).
-// HMODE 0: exact angular-spectrum phase beyond its paraxial part; 1: separable P' with the cross term
-// exp(-i e) as a short series; 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
-template <bool CONJ, int HMODE>
-__device__ __forceinline__ void transfer_tile(float2 (&v)[32], const ColParams& a, const float4* ht, int col, int t)
-{
-    const float4 hx = ht[col];
-    const float2 px = make_float2(hx.x, hx.y);
-    const float kx2 = hx.z;
-    const float cx = a.ccross * kx2;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const float4 hy = ht[t + 32 * i];
-        const float2 q = cmul(px, make_float2(hy.x, hy.y));
-        float2 h;
-        if constexpr (HMODE == 0) {
-            const float k2 = kx2 + hy.z;
-            const float qq = k2 * a.inv_k2;
-            if (qq >= 1.0f) {
-                h = make_float2(0.0f, 0.0f);
-            } else {
-                const float d = 1.0f + sqrtf(1.0f - qq);
-                const float del = __fdividef(a.dcoef * k2 * k2, d * d);
-                const float d2 = del * del;
-                const float cd = 1.0f - d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
-                const float sd = del * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f - d2 * (1.0f / 5040.0f))));
-                h = cmul(q, make_float2(cd, -sd));
-            }
-        } else if constexpr (HMODE == 1) {
-            const float e = cx * hy.z;
-            const float e2 = e * e;
-            h = cmul(q, make_float2(1.0f - e2 * (0.5f - e2 * (1.0f / 24.0f)), -e * (1.0f - e2 * (1.0f / 6.0f))));
-        } else {
-            const float e = cx * hy.z;
-            const float ce = fmaf(-0.5f * e, e, 1.0f);
-            h = make_float2(fmaf(q.x, ce, q.y * e), fmaf(q.y, ce, -q.x * e));
-        }
-        v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
-    }
-}
 
 template <bool CONJ, int HMODE>
 __global__ void __launch_bounds__(ColTma::THREADS, 2)
@@ -190,7 +100,7 @@ __global__ void __launch_bounds__(ColTma::THREADS, 2)
         float2* line = buf + c * ColTma::LS;
         fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
         fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
-        transfer_tile<CONJ, HMODE>(v, a, ht, col, t);
+        transfer_tile<CONJ, HMODE>(v, ht, col, t, a.ccross, a.dcoef, a.inv_k2);
         fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
         if (tid == 0 && tile + (int)gridDim.x < tiles) {
             fence_proxy_async();

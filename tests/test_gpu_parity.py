@@ -500,6 +500,109 @@ def test_prefetching_pass_wait_runs_out_and_is_reported(monkeypatch):
     assert rel_l2(V[0].cpu().numpy(), ref) < TOL
 
 
+def _fused_env(monkeypatch, fused):
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    monkeypatch.setenv("TS_PROP_STREAMS", "1")
+    monkeypatch.setenv("TS_FUSED", "1" if fused else "0")
+
+
+@pytest.mark.parametrize("B,phi_group,source", [(4, 2, True), (8, 8, False), (3, 3, True), (1, 1, False)])
+def test_fused_propagation_matches_oracle_and_per_pass(B, phi_group, source, monkeypatch):
+    # the whole path as one persistent launch (first row pass + S x (column, row) tiles with
+    # per-field dependencies) against the oracle, and against the per-pass launches of the same
+    # kernels; sources generated in the launch or fields read from memory; ragged batches
+    N, dx, S = 1024, 5e-4, 3
+    G = (B + phi_group - 1) // phi_group
+    md = omedium(N, dx)
+    phis = np.stack([np.stack([O.make_screen(md, 1e-14, 62.5, 0, 60, s, g) for s in range(S)]) for g in range(G)])
+    ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
+    rng = np.random.default_rng(61)
+    w0 = [0.01 + 0.002 * b for b in range(B)]
+    U0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    outs = []
+    for fused in (True, False):
+        _fused_env(monkeypatch, fused)
+        plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+        assert plan.tuning_fused()[0] == fused
+        plan.set_sources(w0)
+        U = torch.from_numpy(U0).to(DEV)
+        plan.timing(True, capacity=4)
+        plan.propagate(U, B, phasor=ph, phi_group=phi_group, flags=ts.TS_PROP_SOURCE if source else 0)
+        plan.device_status()
+        assert plan.timing_read(3)[0] == (1 if fused else 0)
+        plan.timing(False)
+        outs.append(U.cpu().numpy())
+    got = outs[0]
+    assert rel_l2(got, outs[1]) < 1e-6
+    for b in range(B):
+        set_phi = np.angle(np.exp(1j * phis[b // phi_group]))
+        src = O.source_gaussian(N, dx, w0[b]) if source else U0[b]
+        ref = O.propagate(md, [62.5] * S, set_phi, src)
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+
+
+def test_fused_propagation_with_regenerated_screens_and_exact_transfer(monkeypatch):
+    # dx = 0.1 mm, dz = 2 m: the exact (non-separable) transfer function; screens regenerated from
+    # the seed into the plan's workspace before the fused launch; two realizations
+    _fused_env(monkeypatch, True)
+    N, dx, S, B = 1024, 1e-4, 2, 2
+    md = omedium(N, dx, l0=2e-4, L0=1.0)
+    plan = ts.Plan(LAM, N, dx, [2.0] * S, [1e-12] * S, l0=2e-4, L0=1.0, max_batch=B)
+    plan.set_sources([2e-3, 3e-3])
+    U = cfield(B, N)
+    plan.timing(True, capacity=4)
+    plan.propagate(U, B, flags=ts.TS_PROP_SOURCE, seed=23, real_base=5)
+    plan.device_status()
+    assert plan.timing_read(3)[0] == 1
+    plan.timing(False)
+    for b, w0 in enumerate((2e-3, 3e-3)):
+        phis = np.stack([O.make_screen(md, 1e-12, 2.0, 0, 23, s, 5 + b) for s in range(S)])
+        ref = O.propagate(md, [2.0] * S, phis, O.source_gaussian(N, dx, w0))
+        assert rel_l2(U[b].cpu().numpy(), ref) < TOL, (b, rel_l2(U[b].cpu().numpy(), ref))
+
+
+def test_fused_propagation_with_the_series_cross_term(monkeypatch):
+    _fused_env(monkeypatch, True)
+    N, dx, S = 1024, 5e-4, 2
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [2500.0] * S, [1e-16] * S, l0=5e-3, L0=10.0, max_batch=1,
+                   flags=ts.TS_PLAN_ALLOW_ALIASING)
+    plan.set_sources([0.05])
+    U = cfield(1, N)
+    plan.propagate(U, 1, flags=ts.TS_PROP_SOURCE, seed=22)
+    plan.device_status()
+    phis = np.stack([O.make_screen(md, 1e-16, 2500.0, 0, 22, s, 0) for s in range(S)])
+    ref = O.propagate(md, [2500.0] * S, phis, O.source_gaussian(N, dx, 0.05))
+    assert rel_l2(U[0].cpu().numpy(), ref) < TOL, rel_l2(U[0].cpu().numpy(), ref)
+
+
+def test_fused_launch_wait_runs_out_and_is_reported(monkeypatch):
+    # TS_PLAN_TEST_STALL: the fused launch issues no input copy, its first input wait runs out (50 ms),
+    # every CTA stops, and the host sees TS_ERR_DEVICE_TIMEOUT; the next plan works
+    _fused_env(monkeypatch, True)
+    N, dx, S = 1024, 5e-4, 2
+    bad = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=2, flags=ts.TS_PLAN_TEST_STALL)
+    bad.set_sources([0.01])
+    ph = torch.ones((S, N, N), dtype=torch.complex64, device=DEV)
+    U = cfield(2, N)
+    bad.propagate(U, 2, phasor=ph, phi_group=2, flags=ts.TS_PROP_SOURCE)
+    with pytest.raises(ts.TsError) as err:
+        bad.device_status()
+    assert err.value.status == 5  # TS_ERR_DEVICE_TIMEOUT
+    bad.device_status()
+    good = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=1)
+    good.set_sources([0.01])
+    V = cfield(1, N)
+    good.propagate(V, 1, flags=ts.TS_PROP_SOURCE, seed=5)
+    good.device_status()
+    md = omedium(N, dx)
+    phis = np.stack([O.make_screen(md, 1e-15, 62.5, 0, 5, s, 0) for s in range(S)])
+    ref = O.propagate(md, [62.5] * S, phis, O.source_gaussian(N, dx, 0.01))
+    assert rel_l2(V[0].cpu().numpy(), ref) < TOL
+
+
 def test_tuning_candidate_table():
     N, dx, S = 1024, 5e-4, 2
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=4)
