@@ -246,13 +246,18 @@ def run_gpu(args):
     # The kernels are timed alone: this pass uses a plan that keeps all fields on one stream, so no
     # launch overlaps another (the timed steps above run the autotuned number of concurrent groups).
     n_prof = min(args.steps, 256)
-    old_env = os.environ.get("TS_PROP_STREAMS")
-    os.environ["TS_PROP_STREAMS"] = "1"
+    # the same kernels as the timed steps (the main plan's autotuner choices), on one stream
+    tune = plan.tuning()
+    pinned = {"TS_PROP_STREAMS": "1", "TS_FFT_E": str(tune[0]), "TS_COL_VARIANT": str(tune[5]),
+              "TS_ROW_VARIANT": str(tune[7]), "TS_FUSED": "1" if fused[0] else "0"}
+    saved = {k: os.environ.get(k) for k in pinned}
+    os.environ.update(pinned)
     prof_plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
-    if old_env is None:
-        del os.environ["TS_PROP_STREAMS"]
-    else:
-        os.environ["TS_PROP_STREAMS"] = old_env
+    for k, v in saved.items():
+        if v is None:
+            del os.environ[k]
+        else:
+            os.environ[k] = v
     prof_plan.set_sources(wl.w0)
     prof_plan.timing(True, capacity=n_prof * (S + 1))
     barrier()
