@@ -10,12 +10,13 @@
 // the launch cannot deadlock for any grid size.  While one field's column pass drains, other
 // fields' row passes already run, so no per-pass launch tail idles the GPU.
 //
-// Each CTA takes its next item when it starts the current one, and issues the next item's input
-// copies (a 64 KiB column tile by four 2-D TMA boxes plus the step's 16 KiB (P, ky^2) table, or eight
-// 8 KiB field rows by bulk copies) as soon as the current item's last shared-memory exchange has been
-// read and the next item's dependency is already met; otherwise it waits for the dependency (bounded)
-// when it gets there.  Row tiles fetch their screen phasor rows with per-warp bulk copies under the
-// second stage of the inverse FFT.
+// Each CTA knows its next item while it runs the current one and issues the next item's input copies
+// (a 64 KiB column tile by four 2-D TMA boxes plus the step's 16 KiB (P, ky^2) table, or one 8 KiB field
+// row per warp by bulk copies) as soon as the buffer is free and the next item's dependency is already
+// met; otherwise it waits for the dependency (bounded) when it gets there.  Row tiles run their eight
+// warps independently: each warp has its own line and mbarrier, fetches its screen phasor row under
+// the second stage of the inverse FFT and, when the next item is also a row tile, its next field row
+// under the second stage of the forward FFT.  Column tiles synchronise the block at their exchanges.
 //
 // Completion: a tile's stores, a block barrier, then (during the CTA's next item, once the stores have
 // had a stage to drain, or at once before any blocking wait) thread 0 fences and adds 1 to the
@@ -49,7 +50,7 @@ struct Fused {
     static constexpr size_t off_buf = off_ht + HT_BYTES;
     static constexpr size_t off_bar = off_buf + sizeof(float2) * W * LSC;
     static constexpr size_t off_int = off_bar + 8 * (1 + WARPS);
-    static constexpr size_t smem = off_int + 16;
+    static constexpr size_t smem = off_int + 4 * (2 + WARPS);
     static_assert(W * LSC >= W * kN && W * LSC >= WARPS * LSR, "tile, lines and exchanges fit the buffer");
     static_assert(off_buf % 128 == 0 && off_ht % 128 == 0 && (LSR * 8) % 16 == 0, "copy alignment");
 };
@@ -66,22 +67,22 @@ __device__ __forceinline__ void item_decode(int it, int B, int& p, int& b, int& 
     tile = rem - b * Fused::TPF;
 }
 
-// thread 0: the input copies of item `it` (phase p, field b, tile) on the CTA's input barrier
-__device__ __forceinline__ void issue_input(const FusedParams& a, const CUtensorMap* map, int p, int b, int tile,
-                                            float2* buf, float4* ht, uint64_t* bin)
+// the input copies of a column tile (thread 0): four 2-D TMA boxes + the step's transfer table
+__device__ __forceinline__ void issue_col(const FusedParams& a, const CUtensorMap* map, int p, int b, int tile,
+                                          float2* buf, float4* ht, uint64_t* bin)
 {
-    if (p & 1) {  // column tile + the step's transfer table
-        const int s = (p - 1) >> 1;
-        mbar_expect_tx(bin, Fused::TILE_BYTES + Fused::HT_BYTES);
+    const int s = (p - 1) >> 1;
+    mbar_expect_tx(bin, Fused::TILE_BYTES + Fused::HT_BYTES);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tma_load_2d(buf + q * 256 * Fused::W, map, 16 * tile, b * kN + q * 256, bin);
-        bulk_load(ht, a.ht + (size_t)s * kN, Fused::HT_BYTES, bin);
-    } else {  // 8 field rows, one per warp line
-        mbar_expect_tx(bin, Fused::TILE_BYTES);
-        const float2* src = a.field + ((size_t)b * kN + (size_t)tile * Fused::WARPS) * kN;
-#pragma unroll
-        for (int w = 0; w < Fused::WARPS; ++w) bulk_load(buf + w * Fused::LSR, src + (size_t)w * kN, kN * 8, bin);
-    }
+    for (int q = 0; q < 4; ++q) tma_load_2d(buf + q * 256 * Fused::W, map, 16 * tile, b * kN + q * 256, bin);
+    bulk_load(ht, a.ht + (size_t)s * kN, Fused::HT_BYTES, bin);
+}
+
+// the input copy of row `w` of a row tile into warp w's line, on warp w's barrier
+__device__ __forceinline__ void issue_row(const FusedParams& a, int b, int tile, int w, float2* buf, uint64_t* bw)
+{
+    mbar_expect_tx(bw + w, kN * 8);
+    bulk_load(buf + w * Fused::LSR, a.field + ((size_t)b * kN + (size_t)tile * Fused::WARPS + w) * kN, kN * 8, bw + w);
 }
 
 template <int HMODE>
@@ -93,28 +94,29 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
     float2* tw = reinterpret_cast<float2*>(sm);
     float4* ht = reinterpret_cast<float4*>(sm + Fused::off_ht);
     float2* buf = reinterpret_cast<float2*>(sm + Fused::off_buf);
-    uint64_t* bin = reinterpret_cast<uint64_t*>(sm + Fused::off_bar);
-    uint64_t* bph = bin + 1;
+    uint64_t* bin = reinterpret_cast<uint64_t*>(sm + Fused::off_bar);  // column-tile input
+    uint64_t* bw = bin + 1;  // per warp: row input, then the phasor row
     int* s_int = reinterpret_cast<int*>(sm + Fused::off_int);  // [0] first item, [1] next item
+    int* row_issued = s_int + 2;  // per warp: the row item whose input row was issued into its line
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int per_phase = a.B * Fused::TPF;
-    const int total = (2 * a.S + 1) * per_phase;
-    // thread-0 state: the item whose input copies are in flight or have landed; the item after the
-    // next one (its fetch is in flight during the current item); the (phase, field) counter of the
-    // last finished tile, signalled once its stores have drained (or before any blocking wait)
-    int issued_for = -1, fetched = 0, pending = -1;
+    const int total = (2 * a.S + 1) * a.B * Fused::TPF;
+    // thread-0 state: the column item whose tile copy is in flight or has landed; the item after the
+    // next one (its fetch is in flight during the current item); the (pass, field) counter of the last
+    // finished tile, signalled once its stores have drained (or before any blocking wait)
+    int col_issued = -1, fetched = 0, pending = -1;
 
     if (tid == 0) {
         mbar_init(bin, 1);
-        for (int w = 0; w < Fused::WARPS; ++w) mbar_init(bph + w, 1);
+        for (int w = 0; w < Fused::WARPS; ++w) mbar_init(bw + w, 1);
         mbar_init_fence();
         s_int[0] = atomicAdd(a.head, 1);
         fetched = atomicAdd(a.head, 1);
     }
+    if (tid < Fused::WARPS) row_issued[tid] = -1;
     stage_twiddles_c<C>(tw, a.tw);
     __syncthreads();
     int cur = s_int[0];
-    uint32_t pin = 0, pph = 0;
+    uint32_t pin = 0, pw = 0;  // parities of the column-tile barrier and of this warp's barrier
 
     auto signal = [&]() {  // thread 0
         if (pending >= 0) {
@@ -123,29 +125,33 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
             pending = -1;
         }
     };
-    // thread 0: input of `nxt` if its dependency is met now (no wait)
-    auto try_prefetch = [&](int nxt) {
-        if (nxt >= total || a.stall) return;
-        int p, b, tile;
-        item_decode(nxt, a.B, p, b, tile);
-        if (p == 0 && a.source) return;
-        if (p > 0 && ld_acquire(a.done + (p - 1) * a.B + b) < Fused::TPF) return;
-        fence_proxy_async_global();
-        fence_proxy_async();
-        issue_input(a, &tmap, p, b, tile, buf, ht, bin);
-        issued_for = nxt;
+    // whether item `it` needs input copies and its dependency is met now (acquire, no wait)
+    auto ready = [&](int it, int& p, int& b, int& tile) {
+        if (it >= total || a.stall) return false;
+        item_decode(it, a.B, p, b, tile);
+        if (p == 0 && a.source) return false;
+        return p == 0 || ld_acquire(a.done + (p - 1) * a.B + b) >= Fused::TPF;
     };
 
     while (cur < total) {
         int p, b, tile;
         item_decode(cur, a.B, p, b, tile);
         const bool needs_input = p > 0 || !a.source;
+        const bool col = (p & 1) != 0;
         int abort_local = 0, err_seen = 0;
         if (tid == 0) {
-            s_int[1] = fetched;               // the next item, fetched during the previous one
-            fetched = atomicAdd(a.head, 1);   // the one after: its latency hides under this item
-            err_seen = ld_relaxed(a.err);     // read at the end of the item
-            if (needs_input && issued_for != cur) {
+            s_int[1] = fetched;              // the next item, fetched during the previous one
+            fetched = atomicAdd(a.head, 1);  // the one after: its latency hides under this item
+            err_seen = ld_relaxed(a.err);    // read at the end of the item
+            bool missing = false;
+            if (needs_input) {
+                if (col) {
+                    missing = col_issued != cur;
+                } else {
+                    for (int w = 0; w < Fused::WARPS; ++w) missing |= row_issued[w] != cur;
+                }
+            }
+            if (missing) {
                 bool ok = true;
                 if (p > 0) {
                     signal();  // never wait while holding an unsignalled tile
@@ -161,8 +167,17 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
                 }
                 if (ok && !a.stall) {
                     fence_proxy_async_global();
-                    issue_input(a, &tmap, p, b, tile, buf, ht, bin);
-                    issued_for = cur;
+                    if (col) {
+                        issue_col(a, &tmap, p, b, tile, buf, ht, bin);
+                        col_issued = cur;
+                    } else {
+                        for (int w = 0; w < Fused::WARPS; ++w) {
+                            if (row_issued[w] != cur) {
+                                issue_row(a, b, tile, w, buf, bw);
+                                row_issued[w] = cur;
+                            }
+                        }
+                    }
                 }
                 if (!ok) {
                     atomicExch(a.err, kErrDepWait);
@@ -170,21 +185,19 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
                 }
             }
         }
-        if (__syncthreads_or(abort_local)) {
-            if (tid == 0 && issued_for == cur) mbar_wait(bin, pin, a.budget);  // a prefetched copy in flight
+        if (__syncthreads_or(abort_local)) {  // copies of this item in flight: wait for them (bounded)
+            if (tid == 0 && col_issued == cur) mbar_wait(bin, pin, a.budget);
+            if (lane == 0 && !col && row_issued[warp] == cur) mbar_wait(bw + warp, pw, a.budget);
             return;
         }
         const int nxt = s_int[1];
-        bool ok = true;
-        if (needs_input) {
-            ok = mbar_wait(bin, pin, a.budget);
-            pin ^= 1u;
-        }
-        bool bad = false;  // this thread's warp saw a phasor-copy wait run out
+        bool bad = false;  // a wait of this thread's warp ran out (the launch then stops)
         float2 v[32];
-        if (p & 1) {
+        if (col) {
             // ---------------- column tile: FFT -> H_s -> IFFT over 8 columns ----------------
             const int c = tid % Fused::W, t = tid / Fused::W, s = (p - 1) >> 1;
+            const bool ok = mbar_wait(bin, pin, a.budget);
+            pin ^= 1u;
             if (ok) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = buf[(t + 32 * i) * Fused::W + c];
@@ -197,19 +210,34 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
                 return;
             }
             float2* line = buf + c * Fused::LSC;
-            const int col = tile * Fused::W + c;
+            const int colx = tile * Fused::W + c;
             fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
             if (tid == 0) signal();  // the previous tile's stores have had a stage to drain
             fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
-            transfer_tile<false, HMODE>(v, ht, col, t, a.ccross[s], a.dcoef[s], a.inv_k2);
+            transfer_tile<false, HMODE>(v, ht, colx, t, a.ccross[s], a.dcoef[s], a.inv_k2);
             fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
-            if (tid == 0) try_prefetch(nxt);
+            if (tid == 0) {  // the whole buffer is free: the next item's input, if it is ready
+                int pn, bn, tn;
+                if (ready(nxt, pn, bn, tn)) {
+                    fence_proxy_async_global();
+                    fence_proxy_async();
+                    if (pn & 1) {
+                        issue_col(a, &tmap, pn, bn, tn, buf, ht, bin);
+                        col_issued = nxt;
+                    } else {
+                        for (int w = 0; w < Fused::WARPS; ++w) {
+                            issue_row(a, bn, tn, w, buf, bw);
+                            row_issued[w] = nxt;
+                        }
+                    }
+                }
+            }
             fft_stage_c<C, 1, +1>(v, line, t, tw, BlockBar());
-            float2* base = a.field + (size_t)b * kN * kN + col;
+            float2* base = a.field + (size_t)b * kN * kN + colx;
 #pragma unroll
             for (int i = 0; i < 32; ++i) base[(size_t)(t + 32 * i) * kN] = v[i];
         } else {
-            // ---------------- row tile: one row per warp ----------------
+            // ---------------- row tile: one row per warp, warps independent ----------------
             float2* line = buf + warp * Fused::LSR;
             const int j = tile * Fused::WARPS + warp;
             float2* row = a.field + ((size_t)b * kN + j) * kN;
@@ -222,12 +250,11 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
                     v[i] = coef < 0.0f ? make_float2(1.0f, 0.0f) : make_float2(expf(-(x * x + y * y) * coef), 0.0f);
                 }
             } else {
-                if (__syncthreads_or(!ok)) {
-                    if (tid == 0) {
-                        atomicExch(a.err, kErrDepWait);
-                        mbar_wait(bin, pin ^ 1u, a.budget);
-                    }
-                    return;
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(bw + warp, pw, a.budget));
+                pw ^= 1u;
+                if (!ok) {
+                    bad = true;
+                    if (lane == 0) mbar_wait(bw + warp, pw ^ 1u, a.budget);
                 }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = line[lane + 32 * i];
@@ -240,16 +267,16 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
                 if (lane == 0) {  // the line is free: the screen phasor row comes in under the next stage
                     const int set = (b + a.phi_off) / a.phi_group;
                     fence_proxy_async();
-                    mbar_expect_tx(bph + warp, kN * 8);
+                    mbar_expect_tx(bw + warp, kN * 8);
                     bulk_load(line, a.phasor + (long long)s * kN * kN + (long long)set * a.set_stride + (size_t)j * kN,
-                              kN * 8, bph + warp);
+                              kN * 8, bw + warp);
                 }
                 fft_stage_c<C, 1, +1>(v, line, lane, tw, WarpBar());
-                const bool okp = __all_sync(0xffffffffu, mbar_wait(bph + warp, pph, a.budget));
-                pph ^= 1u;
+                const bool okp = __all_sync(0xffffffffu, mbar_wait(bw + warp, pw, a.budget));
+                pw ^= 1u;
                 if (!okp) {
                     bad = true;
-                    if (lane == 0) mbar_wait(bph + warp, pph ^ 1u, a.budget);
+                    if (lane == 0) mbar_wait(bw + warp, pw ^ 1u, a.budget);
                 }
                 if (a.phase_sign > 0.0f) {
 #pragma unroll
@@ -262,8 +289,15 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
             }
             const bool out_freq = p < 2 * a.S;
             if (out_freq) fft_stage_c<C, 0, -1>(v, line, lane, tw, WarpBar());
-            __syncthreads();  // every line is free
-            if (tid == 0) try_prefetch(nxt);
+            if (lane == 0) {  // this warp's line is free: its row of the next item, if that is a ready row tile
+                int pn, bn, tn;
+                if (ready(nxt, pn, bn, tn) && !(pn & 1)) {
+                    fence_proxy_async_global();
+                    fence_proxy_async();
+                    issue_row(a, bn, tn, warp, buf, bw);
+                    row_issued[warp] = nxt;
+                }
+            }
             if (out_freq) fft_stage_c<C, 1, -1>(v, line, lane, tw, WarpBar());
 #pragma unroll
             for (int i = 0; i < 32; ++i) row[lane + 32 * i] = v[i];
@@ -273,8 +307,9 @@ __global__ void __launch_bounds__(Fused::THREADS, 2) prop_fused_kernel(const Fus
         if (ab) {
             if (tid == 0) {
                 if (bad) atomicExch(a.err, kErrDepWait);
-                if (issued_for == nxt) mbar_wait(bin, pin, a.budget);  // the prefetched copy in flight
+                if (col_issued == nxt) mbar_wait(bin, pin, a.budget);  // prefetched copies in flight
             }
+            if (lane == 0 && row_issued[warp] == nxt) mbar_wait(bw + warp, pw, a.budget);
             return;
         }
         if (tid == 0) pending = p * a.B + b;
