@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--overlap", action="store_true",
+                    help="synthesise the next step's screens on a second stream while the current step propagates")
     ap.add_argument("--no-split-bf16", action="store_true",
                     help="skip the split-BF16 tensor-core comparison (profiling runs)")
     ap.add_argument("--workload", default="ar-evolution",
@@ -206,11 +208,35 @@ def run_gpu(args):
     real = rank  # each rank evolves its own independent realization
     t_next = [0]
 
-    def step(p=plan):
+    def step_serial(p=plan):
         t = t_next[0]
         p.evolve_screens(spec, None, wl.seed, t, wl.alpha, real=real, phasor=phasor, stream=stream)
         p.propagate(U, B, phasor=phasor, phi_group=B, flags=ts.TS_PROP_SOURCE, stream=stream)
         t_next[0] = t + 1
+
+    # overlapped steps: the screens of step t + 1 are synthesised on their own stream while step t
+    # propagates; the phasors are double-buffered (step t reads buffer t mod 2; the AR state itself
+    # is only touched by the screen stream, in step order)
+    s_scr = torch.cuda.Stream(dev)
+    phasors = [phasor, torch.zeros_like(phasor)] if args.overlap else [phasor]
+    ev_scr = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_prop = [torch.cuda.Event(), torch.cuda.Event()]
+    for ev in ev_prop:
+        ev.record(stream)
+
+    def step_overlap(p=plan):
+        t = t_next[0]
+        k = t % 2
+        s_scr.wait_event(ev_prop[k])  # step t - 2 has finished reading this phasor buffer
+        p.evolve_screens(spec, None, wl.seed, t, wl.alpha, real=real, phasor=phasors[k], stream=s_scr)
+        ev_scr[k].record(s_scr)
+        stream.wait_event(ev_scr[k])
+        p.propagate(U, B, phasor=phasors[k], phi_group=B, flags=ts.TS_PROP_SOURCE, stream=stream)
+        ev_prop[k].record(stream)
+        t_next[0] = t + 1
+
+    def step(p=plan):
+        (step_overlap if args.overlap else step_serial)(p)
 
     def barrier():
         if world > 1:
@@ -237,6 +263,7 @@ def run_gpu(args):
     e0.record(stream)
     for _ in range(args.steps):
         step()
+    stream.wait_stream(s_scr)
     e1.record(stream)
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
@@ -294,9 +321,9 @@ def run_gpu(args):
     traffic, traffic_warm = load_traffic(dom)
     roof = {"bound": "hbm", "kernel": dom, "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": round(dk["achieved_gbs"] / peak, 4), "traffic": traffic,
-            "traffic_note": "ncu dram read + write per 8-field launch, cold caches (ncu flushes before replay); "
-                            "mid-pipeline with warm caches a 4-field launch moves traffic_warm_4_fields bytes: the "
-                            "fields stay L2-resident between the passes",
+            "traffic_note": "ncu dram read + write per 8-field launch, cold caches (ncu flushes before replay), from the "
+                            "committed capture while the kernel's sources still hash to it; in the running pipeline "
+                            "the fields stay L2-resident between the passes",
             "traffic_warm_4_fields": traffic_warm, "peak_source": peak_src,
             "timing": "per-launch CUDA events on the launching stream, each kernel alone (one stream)",
             "kernels": per_kernel}
@@ -392,6 +419,7 @@ def run_gpu(args):
         "config": {"workload": wl.name, "N": N, "dx": wl.dx, "L": wl.L, "screens": S, "beams": B,
                    "cn2": wl.cn2[0], "alpha": wl.alpha, "field_screen_steps_per_step": B * S,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "screens_overlap_propagation": bool(args.overlap),
                    "autotune": dict(zip(("points_per_thread", "us_e16", "us_e32", "streams", "us_streams_1_2_4",
                                          "col_variant", "us_e32_warp_columns", "row_variant",
                                          "us_e32_shared_phasor_rows"),

@@ -126,7 +126,9 @@ __device__ __forceinline__ float2 twiddle_const(float2 v)
 
 // In-register DFT of length R on a compact array x[0..R-1] (natural order in and out),
 // X[k] = sum_n x[n] exp(SIGN 2 pi i n k / R).  Recursive radix-2 decimation in time; every index
-// is a compile-time constant after unrolling, so x stays in registers.
+// is a compile-time constant after unrolling, so x stays in registers.  In the butterflies, a twiddle
+// of +-i becomes scalar adds with the sign folded in, and one of the odd multiples of pi/4 becomes
+// t = (+-o.x -+ o.y, ...) followed by e +- t / sqrt(2) as packed FMAs (2 instructions saved each).
 template <int R, int SIGN>
 struct Dft {
     __device__ __forceinline__ static void run(float2* x)
@@ -145,9 +147,25 @@ struct Dft {
     __device__ __forceinline__ static void combine(float2* x, const float2* e, const float2* o)
     {
         if constexpr (K < R / 2) {
-            const float2 t = twiddle_const<R, K, SIGN>(o[K]);
-            x[K] = cadd(e[K], t);
-            x[K + R / 2] = csub(e[K], t);
+            constexpr int k32 = (K * 32 / R) & 31;
+            if constexpr (k32 == 8 || k32 == 24) {
+                // o * (+-i): scalar adds with the sign folded in
+                constexpr float sg = (k32 == 8) == (SIGN > 0) ? 1.0f : -1.0f;  // o * (sg i) = (-sg o.y, sg o.x)
+                x[K] = make_float2(e[K].x - sg * o[K].y, e[K].y + sg * o[K].x);
+                x[K + R / 2] = make_float2(e[K].x + sg * o[K].y, e[K].y - sg * o[K].x);
+            } else if constexpr ((k32 & 7) == 4) {
+                // W = c (sr + i si), |c| = 1/sqrt(2): W o = c t, t = (sr o.x - si o.y, sr o.y + si o.x)
+                constexpr double wr = cos32(k32), wi = SIGN * sin32(k32);
+                constexpr float sr = wr > 0 ? 1.0f : -1.0f, si = wi > 0 ? 1.0f : -1.0f;
+                constexpr float c = 0.70710678118654752f;
+                const float2 t = make_float2(sr * o[K].x - si * o[K].y, sr * o[K].y + si * o[K].x);
+                x[K] = __ffma2_rn(make_float2(c, c), t, e[K]);
+                x[K + R / 2] = __ffma2_rn(make_float2(-c, -c), t, e[K]);
+            } else {
+                const float2 t = twiddle_const<R, K, SIGN>(o[K]);
+                x[K] = cadd(e[K], t);
+                x[K + R / 2] = csub(e[K], t);
+            }
             combine<K + 1>(x, e, o);
         }
     }
