@@ -41,13 +41,23 @@ def build(force: bool = False) -> str:
 
 
 class Medium(C.Structure):
-    """Mirror of ``orc_medium``: wavelength, mean index, inner/outer scale, grid N and dx."""
+    """Mirror of ``orc_medium``: wavelength, mean index, inner/outer scale, grid N and dx, and the
+    power law alpha and constant A of the index PSD (0 = Kolmogorov 11/3 and 0.033)."""
     _fields_ = [("lambda_", C.c_double), ("n0", C.c_double), ("l0", C.c_double), ("L0", C.c_double),
-                ("N", C.c_int), ("dx", C.c_double)]
+                ("N", C.c_int), ("dx", C.c_double), ("alpha", C.c_double), ("A", C.c_double)]
 
 
-def medium(lam, N, dx, n0=1.0, l0=0.0, L0=0.0) -> Medium:
-    return Medium(float(lam), float(n0), float(l0), float(L0 if np.isfinite(L0) else 0.0), int(N), float(dx))
+def medium(lam, N, dx, n0=1.0, l0=0.0, L0=0.0, alpha=0.0, A=0.0) -> Medium:
+    """A medium with the modified von Karman PSD (S17) or, with alpha (Table S1) and A given, the
+    power law A Cn^2 (kappa^2 + kappa0^2)^(-alpha/2) exp(-kappa^2/kappa_m^2) (S12, S15)."""
+    return Medium(float(lam), float(n0), float(l0), float(L0 if np.isfinite(L0) else 0.0), int(N), float(dx),
+                  float(alpha), float(A))
+
+
+def power_law_constant(alpha) -> float:
+    """A(alpha) = Gamma(alpha - 1) cos(pi alpha / 2) / (4 pi^2): the constant for which the index PSD
+    A Cn^2 kappa^-alpha has the structure function Cn^2 r^(alpha - 3) (3 < alpha < 5)."""
+    return _load().orc_power_law_constant(float(alpha))
 
 
 def _load():
@@ -64,6 +74,7 @@ def _load():
                 "orc_fft": (None, [i, p, i]),
                 "orc_fft2": (None, [i, p, i]),
                 "orc_phase_psd": (d, [pm, d, d, d]),
+                "orc_power_law_constant": (d, [d]),
                 "orc_psd_amplitude": (None, [pm, d, d, p]),
                 "orc_sh_amplitude": (None, [pm, d, d, p]),
                 "orc_sh_screen": (None, [pm, p, p]),

@@ -17,7 +17,8 @@
  *   - Spectral index map f(n) = n for n < N/2, else n - N; kappa = (2 pi / (N dx)) * f(n).
  *   - Complex Gaussian noise N_c(0,1): real and imaginary parts each N(0,1) (Eq. 2, S16).
  *   - The phase PSD is Phi_phi = 2 pi k^2 dz * 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6)
- *     exp(-kappa^2/kappa_m^2), kappa0 = 2 pi / L0, kappa_m = 2 pi / l0 (S14, S17, S18, angular).
+ *     exp(-kappa^2/kappa_m^2), kappa0 = 2 pi / L0, kappa_m = 2 pi / l0 (S14, S17, S18, angular);
+ *     other media of Table S1 replace 11/3 by their power law alpha and 0.033 by a constant A.
  *   - H = exp(-i dz kappa^2 / (k + sqrt(k^2 - kappa^2))) = H_as * exp(-i k dz)  (Sec. 2.4; the
  *     global piston exp(i k dz) is dropped), 0 in the evanescent region.
  *
@@ -178,6 +179,8 @@ typedef struct {
     double L0;     /* outer scale [m]; <= 0 or inf -> no outer scale */
     int N;         /* grid size (power of two) */
     double dx;     /* grid spacing [m] */
+    double alpha;  /* power law of the index PSD, Phi_n ~ kappa^-alpha (Table S1); <= 0 -> 11/3 */
+    double A;      /* constant of the index PSD; <= 0 -> 0.033 (Kolmogorov, S17 with S18) */
 } orc_medium;
 
 static double kspace(int N, int n) { return (double)(n < N / 2 ? n : n - N); }
@@ -185,13 +188,32 @@ static double dkappa(const orc_medium* md) { return 2.0 * M_PI / ((double)md->N 
 static double wavenumber(const orc_medium* md) { return 2.0 * M_PI * md->n0 / md->lambda; }
 
 /* Modified von Karman refractive-index PSD, S17 with kappa_m = 2 pi / l0 and kappa0 = 2 pi / L0,
- * written through Cn^2 (S18): Phi_n = 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6) exp(-kappa^2/kappa_m^2). */
+ * written through Cn^2 (S18): Phi_n = 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6) exp(-kappa^2/kappa_m^2).
+ * For another medium of Table S1 the power law is Phi_n ~ kappa^-alpha (S12), alpha = beta + 3
+ * (S11), with the same inner / outer-scale modification:
+ *   Phi_n = A Cn^2 (kappa^2 + kappa0^2)^(-alpha/2) exp(-kappa^2/kappa_m^2).
+ * The paper gives the law up to its constant; A is the caller's (orc_power_law_constant gives the
+ * one for which Cn^2 is the index structure constant, D_n(r) = Cn^2 r^(alpha-3)). */
+static double psd_alpha(const orc_medium* md) { return md->alpha > 0.0 ? md->alpha : 11.0 / 3.0; }
+static double psd_const(const orc_medium* md) { return md->A > 0.0 ? md->A : 0.033; }
+
 static double phi_n(const orc_medium* md, double cn2, double kappa2)
 {
     double k0sq = (md->L0 > 0.0 && isfinite(md->L0)) ? pow(2.0 * M_PI / md->L0, 2.0) : 0.0;
     double kmsq = md->l0 > 0.0 ? pow(2.0 * M_PI / md->l0, 2.0) : INFINITY;
     double roll = isinf(kmsq) ? 1.0 : exp(-kappa2 / kmsq);
-    return 0.033 * cn2 * pow(kappa2 + k0sq, -11.0 / 6.0) * roll;
+    return psd_const(md) * cn2 * pow(kappa2 + k0sq, -psd_alpha(md) / 2.0) * roll;
+}
+
+/* The constant A(alpha) of a power-law index PSD A Cn^2 kappa^-alpha whose structure function is
+ * D_n(r) = Cn^2 r^(alpha - 3) (3 < alpha < 5), where D_n(r) = 8 pi int (1 - sin(kappa r)/(kappa r))
+ * Phi_n(kappa) kappa^2 dkappa: the published non-Kolmogorov constant
+ *   A(alpha) = Gamma(alpha - 1) cos(pi alpha / 2) / (4 pi^2)
+ * (Toselli, Andrews, Phillips, Ferrero 2007), 0.0330 at alpha = 11/3 (the Kolmogorov 0.033).  Pinned
+ * in the tests against the defining integral, evaluated numerically. */
+double orc_power_law_constant(double alpha)
+{
+    return tgamma(alpha - 1.0) * cos(M_PI * alpha / 2.0) / (4.0 * M_PI * M_PI);
 }
 
 /* Phase PSD of one screen covering an interval dz: S14, Phi_phi = 2 pi k^2 dz Phi_n. */
