@@ -99,6 +99,21 @@ typedef struct ts_plan_s* ts_plan;
 ts_status ts_plan_create(ts_plan* plan, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
                          int sh_levels, int max_batch, int flags);
 
+/* ts_plan_create for another medium of Table S1: the refractive-index PSD is the power law
+ *   Phi_n(kappa) = A Cn^2 (kappa^2 + kappa0^2)^(-alpha/2) exp(-kappa^2 / kappa_m^2)   (S12, S15, S17)
+ * with alpha = beta + 3 (S11): atmosphere 11/3 (Kolmogorov; ts_plan_create uses alpha = 11/3,
+ * A = 0.033), general atmosphere 3..4, oceanic 11/3..5, biological tissue 4.28..4.41.  The paper gives
+ * the law up to its constant; ts_power_law_constant(alpha) returns the one for which Cn^2 is the
+ * index structure constant (D_n(r) = Cn^2 r^(alpha - 3)).  Screens, subharmonics and AR evolution
+ * all use this PSD.  Errors as ts_plan_create, plus TS_ERR_INVALID_ARG for alpha outside (3, 5) or
+ * A not finite and > 0. */
+ts_status ts_plan_create_psd(ts_plan* plan, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
+                             int sh_levels, int max_batch, int flags, double alpha, double A);
+
+/* A(alpha) = Gamma(alpha - 1) cos(pi alpha / 2) / (4 pi^2) for 3 < alpha < 5 (0.0330 at 11/3), the
+ * published non-Kolmogorov constant; NaN outside that range.  Host-only. */
+double ts_power_law_constant(double alpha);
+
 /* Device status of a plan: waits for all work on the device, then returns TS_ERR_DEVICE_TIMEOUT
  * (and clears the flag) if a bounded device wait of its passes ran out of its one-second budget since
  * the last call -- a tensor-core pass (TS_PLAN_SPLIT_BF16) waiting for its MMAs, or a prefetching

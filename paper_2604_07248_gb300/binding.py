@@ -58,6 +58,9 @@ class Path(C.Structure):
 _P, _I, _D, _U32, _U64, _I64 = C.c_void_p, C.c_int, C.c_double, C.c_uint32, C.c_uint64, C.c_int64
 SIGNATURES = {
     "ts_plan_create": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I]),
+    "ts_plan_create_psd": (_I, [C.POINTER(_P), C.POINTER(Medium), C.POINTER(Grid), C.POINTER(Path), _I, _I, _I, _D,
+                                _D]),
+    "ts_power_law_constant": (_D, [_D]),
     "ts_plan_destroy": (_I, [_P]),
     "ts_plan_device_status": (_I, [_P]),
     "ts_plan_set_loss_scale": (_I, [_P, _D]),
@@ -226,10 +229,18 @@ def tc_dft32(x, X, sign=-1, layout=0, err=None, timeout_s=1.0, stream=None):
     return err
 
 
-class Plan:
-    """One medium + grid + path on the current CUDA device (ts_plan)."""
+def power_law_constant(alpha: float) -> float:
+    """A(alpha) of the power-law index PSD A Cn^2 kappa^-alpha (ts_power_law_constant; 0.0330 at 11/3)."""
+    return load().ts_power_law_constant(float(alpha))
 
-    def __init__(self, lam, N, dx, dz, cn2, n0=1.0, l0=0.0, L0=0.0, sh_levels=0, max_batch=1, flags=0):
+
+class Plan:
+    """One medium + grid + path on the current CUDA device (ts_plan).  With `alpha` (and optionally
+    `A`; default ts_power_law_constant(alpha)) the medium's index PSD is the power law of Table S1
+    (ts_plan_create_psd), else the Kolmogorov modified von Karman PSD."""
+
+    def __init__(self, lam, N, dx, dz, cn2, n0=1.0, l0=0.0, L0=0.0, sh_levels=0, max_batch=1, flags=0,
+                 alpha=None, A=None):
         lib = load()
         dz = [float(x) for x in dz]
         cn2 = [float(x) for x in cn2]
@@ -245,8 +256,14 @@ class Plan:
         cna = (C.c_double * len(cn2))(*cn2)
         path = Path(len(dz), dza, cna)
         h = C.c_void_p()
-        _check(lib.ts_plan_create(C.byref(h), C.byref(med), C.byref(grid), C.byref(path), int(sh_levels),
-                                  int(max_batch), int(flags)), "ts_plan_create")
+        if alpha is None and A is None:
+            _check(lib.ts_plan_create(C.byref(h), C.byref(med), C.byref(grid), C.byref(path), int(sh_levels),
+                                      int(max_batch), int(flags)), "ts_plan_create")
+        else:
+            a = 11.0 / 3.0 if alpha is None else float(alpha)
+            A = float(A) if A is not None else lib.ts_power_law_constant(a)
+            _check(lib.ts_plan_create_psd(C.byref(h), C.byref(med), C.byref(grid), C.byref(path), int(sh_levels),
+                                          int(max_batch), int(flags), a, A), "ts_plan_create_psd")
         self._h = h
 
     @property

@@ -41,12 +41,13 @@ bool supported_N(int N) { return N == 128 || N == 256 || N == 512 || N == 1024 |
 
 double wavenumber(const ts_medium* m) { return 2.0 * M_PI * m->n0 / m->lambda; }
 
-// Phi_phi(kappa) = 2 pi k^2 dz 0.033 Cn^2 (kappa^2 + kappa0^2)^(-11/6) exp(-kappa^2 / kappa_m^2)   (S14, S17)
+// Phi_phi(kappa) = 2 pi k^2 dz A Cn^2 (kappa^2 + kappa0^2)^(-alpha/2) exp(-kappa^2 / kappa_m^2)
+// (S14, S17; A = 0.033 and alpha = 11/3 for Kolmogorov, the power law of another medium per S12, S15)
 double phase_psd(const Plan& p, double cn2, double dz, double k2)
 {
     const double k0sq = (p.L0 > 0.0 && std::isfinite(p.L0)) ? std::pow(2.0 * M_PI / p.L0, 2.0) : 0.0;
     const double roll = p.l0 > 0.0 ? std::exp(-k2 / std::pow(2.0 * M_PI / p.l0, 2.0)) : 1.0;
-    return 2.0 * M_PI * p.k * p.k * dz * 0.033 * cn2 * std::pow(k2 + k0sq, -11.0 / 6.0) * roll;
+    return 2.0 * M_PI * p.k * p.k * dz * p.psd_A * cn2 * std::pow(k2 + k0sq, -p.psd_alpha / 2.0) * roll;
 }
 
 template <class T>
@@ -554,10 +555,25 @@ double ts_max_step(const ts_medium* m, const ts_grid* g)
     return 0.5 * g->N * g->dx * std::sqrt(k * k - kmax * kmax) / kmax;
 }
 
+double ts_power_law_constant(double alpha)
+{
+    if (!(alpha > 3.0 && alpha < 5.0)) return std::nan("");
+    return std::tgamma(alpha - 1.0) * std::cos(M_PI * alpha / 2.0) / (4.0 * M_PI * M_PI);
+}
+
 ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
                          int sh_levels, int max_batch, int flags)
 {
+    return ts_plan_create_psd(out, medium, grid, path, sh_levels, max_batch, flags, 11.0 / 3.0, 0.033);
+}
+
+ts_status ts_plan_create_psd(ts_plan* out, const ts_medium* medium, const ts_grid* grid, const ts_path* path,
+                             int sh_levels, int max_batch, int flags, double alpha, double A)
+{
     set_error("");
+    if (out) *out = nullptr;
+    if (!(alpha > 3.0 && alpha < 5.0) || !(A > 0.0) || !std::isfinite(A))
+        return fail(TS_ERR_INVALID_ARG, "power law alpha must lie in (3, 5) and A must be finite and > 0");
     if (!out || !medium || !grid || !path) return fail(TS_ERR_INVALID_ARG, "null pointer argument");
     *out = nullptr;
     if (!supported_N(grid->N)) return fail(TS_ERR_INVALID_ARG, "N must be one of 128, 256, 512, 1024, 2048");
@@ -571,6 +587,8 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         return fail(TS_ERR_UNSUPPORTED, "TS_PLAN_SPLIT_BF16 is implemented for N = 1024 (32 x 32 tensor-core DFTs)");
 
     Plan tmp;
+    tmp.psd_alpha = alpha;
+    tmp.psd_A = A;
     tmp.N = grid->N;
     tmp.dx = grid->dx;
     tmp.S = path->n_screens;
@@ -674,9 +692,10 @@ ts_status ts_plan_create(ts_plan* out, const ts_medium* medium, const ts_grid* g
         free_plan(p);
         return st;
     }
-    // per-screen amplitudes: s(kappa) = amp_s g(kappa), amp_s = sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
+    // per-screen amplitudes: s(kappa) = amp_s g(kappa), amp_s = sqrt(2 pi k^2 dz A Cn^2) dkappa
     float amp[kMaxScreens];
-    for (int s = 0; s < S; ++s) amp[s] = (float)(std::sqrt(2.0 * M_PI * p->k * p->k * p->dz[s] * 0.033 * p->cn2[s]) * p->dk);
+    for (int s = 0; s < S; ++s)
+        amp[s] = (float)(std::sqrt(2.0 * M_PI * p->k * p->k * p->dz[s] * p->psd_A * p->cn2[s]) * p->dk);
     ok(cudaMemcpy(p->amp, amp, sizeof(float) * S, cudaMemcpyHostToDevice));
     if (sh_levels) {
         // b[p][q] = sqrt(Phi_phi(kappa_pq)) dkappa / 3^p, kappa_pq = (n', m') dkappa / 3^p   (Eq. 2)

@@ -30,6 +30,8 @@ struct Plan {
     int max_batch = 0;
     int screen_chunk = 0;  // screens per synthesis launch (workspace rows)
     double lambda = 0, n0 = 1, l0 = 0, L0 = 0, dx = 0, k = 0, dk = 0;
+    double psd_alpha = 11.0 / 3.0;  // index PSD A Cn^2 (kappa^2 + kappa0^2)^(-alpha/2) exp(-kappa^2/kappa_m^2)
+    double psd_A = 0.033;
     double dz[kMaxScreens] = {};
     double cn2[kMaxScreens] = {};
     int n_src = 0;
@@ -97,7 +99,7 @@ ts_status cuda_check(cudaError_t e, const char* where);
 cudaError_t build_tables(Plan& p);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int n, uint32_t* out, cudaStream_t st);
 cudaError_t launch_twiddles(int N, float2* tw, cudaStream_t st);
-cudaError_t launch_psd_shape(int N, float* g, double dk, double L0, double l0, cudaStream_t st);
+cudaError_t launch_psd_shape(int N, float* g, double dk, double L0, double l0, cudaStream_t st);  // Kolmogorov
 // one screen (no subharmonics) from caller-provided tables and intermediate buffer
 cudaError_t launch_screen_raw(int N, const float2* tw, const float* g, const float* amp, float2* y, uint64_t seed,
                               int screen, uint32_t real, float* phi, cudaStream_t st);

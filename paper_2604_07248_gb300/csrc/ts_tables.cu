@@ -41,9 +41,10 @@ __global__ void paraxial_kernel(float2* P, const double* dz, int S, int N, doubl
     }
 }
 
-// PSD shape g = (kappa^2 + kappa0^2)^(-11/12) exp(-kappa^2 / (2 kappa_m^2)), g(0) = 0, so that
-// s(kappa) = sqrt(Phi_phi) dkappa = amp_s g (S14, S16, S17).
-__global__ void psd_shape_kernel(float* g, int N, double dk, double k0sq, double inv_kmsq)
+// PSD shape g = (kappa^2 + kappa0^2)^expo exp(-kappa^2 / (2 kappa_m^2)), g(0) = 0, expo = -alpha/4
+// (-11/12 for Kolmogorov), so that s(kappa) = sqrt(Phi_phi) dkappa = amp_s g (S14, S16, S17; power
+// law of Table S1 / S15).
+__global__ void psd_shape_kernel(float* g, int N, double dk, double k0sq, double inv_kmsq, double expo)
 {
     const size_t total = (size_t)N * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
@@ -51,7 +52,7 @@ __global__ void psd_shape_kernel(float* g, int N, double dk, double k0sq, double
         const double kx = dk * kidx(n, N), ky = dk * kidx(m, N);
         const double k2 = kx * kx + ky * ky;
         double v = 0.0;
-        if (m != 0 || n != 0) v = pow(k2 + k0sq, -11.0 / 12.0) * exp(-0.5 * k2 * inv_kmsq);
+        if (m != 0 || n != 0) v = pow(k2 + k0sq, expo) * exp(-0.5 * k2 * inv_kmsq);
         g[idx] = (float)v;
     }
 }
@@ -162,7 +163,7 @@ cudaError_t build_tables(Plan& p)
 
     const double k0sq = (p.L0 > 0.0 && isfinite(p.L0)) ? (2.0 * M_PI / p.L0) * (2.0 * M_PI / p.L0) : 0.0;
     const double inv_kmsq = p.l0 > 0.0 ? 1.0 / ((2.0 * M_PI / p.l0) * (2.0 * M_PI / p.l0)) : 0.0;
-    psd_shape_kernel<<<1024, 256>>>(p.g, p.N, p.dk, k0sq, inv_kmsq);
+    psd_shape_kernel<<<1024, 256>>>(p.g, p.N, p.dk, k0sq, inv_kmsq, -p.psd_alpha / 4.0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (p.sh_levels > 0) {
         sh_basis_kernel<<<1, 256>>>(p.shx, p.shy, p.shy_mean, p.N, p.dk, p.dx);
@@ -188,7 +189,7 @@ cudaError_t launch_psd_shape(int N, float* g, double dk, double L0, double l0, c
 {
     const double k0sq = (L0 > 0.0 && isfinite(L0)) ? (2.0 * M_PI / L0) * (2.0 * M_PI / L0) : 0.0;
     const double inv_kmsq = l0 > 0.0 ? 1.0 / ((2.0 * M_PI / l0) * (2.0 * M_PI / l0)) : 0.0;
-    psd_shape_kernel<<<1024, 256, 0, st>>>(g, N, dk, k0sq, inv_kmsq);
+    psd_shape_kernel<<<1024, 256, 0, st>>>(g, N, dk, k0sq, inv_kmsq, -11.0 / 12.0);
     return cudaGetLastError();
 }
 

@@ -58,14 +58,27 @@ def test_max_step_is_eq7_reading():
     (dict(max_batch=0), 1),
     (dict(dz=[1000.0], cn2=[1e-15]), 2),  # above the Eq. 7 limit of 330 m at N = 128, dx = 2 mm
     (dict(flags=bd.TS_PLAN_SPLIT_BF16), 6),  # the tensor-core passes exist for N = 1024 only
+    (dict(alpha=3.0), 1),  # power law outside (3, 5)
+    (dict(alpha=5.2), 1),
+    (dict(alpha=4.3, A=-1.0), 1),
 ])
 def test_plan_rejects_bad_arguments_before_touching_the_gpu(kw, status):
-    args = dict(lam=1.55e-6, N=128, dx=2e-3, dz=[200.0], cn2=[1e-15], sh_levels=0, max_batch=1, flags=0)
+    args = dict(lam=1.55e-6, N=128, dx=2e-3, dz=[200.0], cn2=[1e-15], sh_levels=0, max_batch=1, flags=0,
+                alpha=None, A=None)
     args.update(kw)
     with pytest.raises(bd.TsError) as ei:
         bd.Plan(args["lam"], args["N"], args["dx"], args["dz"], args["cn2"], sh_levels=args["sh_levels"],
-                max_batch=args["max_batch"], flags=args["flags"])
+                max_batch=args["max_batch"], flags=args["flags"], alpha=args["alpha"], A=args["A"])
     assert ei.value.status == status
+
+
+def test_power_law_constant_host_function():
+    # the library's A(alpha) (host code) against the oracle's, which the oracle tests pin to the
+    # defining structure-function integral; NaN outside (3, 5)
+    import oracle as O
+    for a in (3.1, 3.5, 11 / 3, 4.0, 4.3, 4.41, 4.9):
+        assert abs(bd.power_law_constant(a) / O.power_law_constant(a) - 1) < 1e-14
+    assert np.isnan(bd.power_law_constant(3.0)) and np.isnan(bd.power_law_constant(5.0))
 
 
 def test_status_strings_and_null_handling():
