@@ -144,13 +144,14 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
                          float* us_streams, int* col_variant, float* us_e32_warp_columns, int* row_variant,
                          float* us_e32_shared_phasor_rows);
 
-/* The autotuner's whole candidate table: *n receives the number of candidates (7); for the first
+/* The autotuner's whole candidate table: *n receives the number of candidates (8); for the first
  * min(max, *n) of them, points_per_thread[c] (16 or 32), col_variant[c] (0: a column line shared by
- * four warps; 1: one warp per column, tile staged through shared memory; 2: persistent CTAs whose next
- * 8-column tile arrives by TMA while the current one is transformed), row_variant[c] (0: each CTA
+ * four warps; 1: one warp per column, tile staged through shared memory; 2 / 3: persistent CTAs (two /
+ * four per SM) whose next 8- / 4-column tile arrives by TMA while the current one is transformed),
+ * row_variant[c] (0: each CTA
  * reads its screen rows; 1: phasor rows shared by the CTA's fields; 2: persistent warps that prefetch
  * their next field row and the screen phasor row with bulk asynchronous copies) and us[c], the timed
- * cost in microseconds of one column + one row pass (0 = not timed).  Variants 1 and 2 exist for
+ * cost in microseconds of one column + one row pass (0 = not timed).  Variants 1 to 3 exist for
  * N = 1024 at 32 points per thread.  Output arrays may be NULL.  Host-only; no device work. */
 ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
                                     int* row_variant, float* us);

@@ -79,20 +79,21 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// v[i] (frequency m = t + 32 i of column col) *= H or conj(H).  ht[m] = (P(m), ky(m)^2).
-// HMODE 0: exact angular-spectrum phase beyond its paraxial part; 1: separable P' with the cross term
-// exp(-i e) as a short series; 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
-template <bool CONJ, int HMODE>
-__device__ __forceinline__ void transfer_tile(float2 (&v)[32], const float4* ht, int col, int t, float ccross,
-                                              float dcoef, float inv_k2)
+// v[i] (frequency m = t + 32 i of column col) *= H or conj(H), with tab(m) = (P(m), ky(m)^2, -) read
+// from the caller's shared-memory table (whatever its layout).  HMODE 0: exact angular-spectrum phase
+// beyond its paraxial part; 1: separable P' with the cross term exp(-i e) as a short series;
+// 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
+template <bool CONJ, int HMODE, class Tab>
+__device__ __forceinline__ void transfer_tile_tab(float2 (&v)[32], Tab tab, int col, int t, float ccross,
+                                                  float dcoef, float inv_k2)
 {
-    const float4 hx = ht[col];
+    const float4 hx = tab(col);
     const float2 px = make_float2(hx.x, hx.y);
     const float kx2 = hx.z;
     const float cx = ccross * kx2;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        const float4 hy = ht[t + 32 * i];
+        const float4 hy = tab(t + 32 * i);
         const float2 q = cmul(px, make_float2(hy.x, hy.y));
         float2 h;
         if constexpr (HMODE == 0) {
@@ -119,6 +120,13 @@ __device__ __forceinline__ void transfer_tile(float2 (&v)[32], const float4* ht,
         }
         v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
     }
+}
+
+template <bool CONJ, int HMODE>
+__device__ __forceinline__ void transfer_tile(float2 (&v)[32], const float4* ht, int col, int t, float ccross,
+                                              float dcoef, float inv_k2)
+{
+    transfer_tile_tab<CONJ, HMODE>(v, [ht](int m) { return ht[m]; }, col, t, ccross, dcoef, inv_k2);
 }
 
 }  // namespace async

@@ -17,10 +17,10 @@ constexpr int kShVectors = 7;   // V0, (Vc_p, Vs_p) for p = 1..3
 
 // autotuner candidates of the propagation passes: (points per thread, column variant, row variant);
 // variants other than 0 exist for N = 1024 at 32 points per thread
-constexpr int kTuneCand = 7;
-constexpr int kCandE[kTuneCand] = {16, 32, 32, 32, 32, 32, 32};
-constexpr int kCandCol[kTuneCand] = {0, 0, 1, 0, 2, 0, 2};
-constexpr int kCandRow[kTuneCand] = {0, 0, 0, 1, 0, 2, 2};
+constexpr int kTuneCand = 8;
+constexpr int kCandE[kTuneCand] = {16, 32, 32, 32, 32, 32, 32, 32};
+constexpr int kCandCol[kTuneCand] = {0, 0, 1, 0, 2, 0, 2, 3};
+constexpr int kCandRow[kTuneCand] = {0, 0, 0, 1, 0, 2, 2, 2};
 
 struct Plan {
     int device = 0;
@@ -47,8 +47,8 @@ struct Plan {
     long long tc_budget = 0;   // clock64 cycles a bounded device wait may take (tensor-core and prefetching passes)
     bool test_stall = false;   // TS_PLAN_TEST_STALL: prefetching passes skip their first copy
     int tc_col_groups = 1;     // tensor-core column tiles: 1 = 4 columns (4 CTAs / SM), 2 = 8 columns (2 CTAs / SM)
-    int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column, 2 = persistent
-                               // CTAs with TMA-prefetched tiles (1 and 2: N = 1024, E = 32)
+    int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column, 2 / 3 =
+                               // persistent CTAs with TMA-prefetched 8- / 4-column tiles (1-3: N = 1024, E = 32)
     int row_variant = 0;       // row pass: 0 = per-CTA screen rows, 1 = phasor rows shared by the CTA's fields,
                                // 2 = persistent warps with bulk-copy prefetch of rows and phasor rows
     float tune_us[8] = {};     // autotuner timings of one column + row pass per candidate (kCandE/Col/Row)

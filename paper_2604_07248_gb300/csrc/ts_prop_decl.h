@@ -47,8 +47,8 @@ struct ColParams {
 template <int N>
 cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B, cudaStream_t st);
 // variant 0: column lines shared by several warps (block synchronisation); variant 1 (N = 1024,
-// E = 32): one warp per column, tile staged through shared memory; variant 2 (N = 1024, E = 32):
-// persistent CTAs whose next 8-column tile arrives by TMA while the current one is transformed
+// E = 32): one warp per column, tile staged through shared memory; variant 2 / 3 (N = 1024, E = 32):
+// persistent CTAs whose next 8- / 4-column tile arrives by TMA while the current one is transformed
 template <int N>
 cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st);
 template <int N>
@@ -85,7 +85,8 @@ cudaError_t prepare_prop_fused_1024();
 cudaError_t build_ht_table(float4* ht, const float2* P, int S, double dk, cudaStream_t st);
 
 // the TMA-prefetching passes (ts_prop_tma.cu); cudaErrorNotSupported when the arguments do not fit them
-cudaError_t col_pass_tma_1024(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
+// w = columns per CTA (8: two CTAs per SM, 4: four CTAs per SM)
+cudaError_t col_pass_tma_1024(int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
 cudaError_t row_pass_tma_1024(int flags, const RowParams& rp, int B, cudaStream_t st);
 cudaError_t prepare_prop_tma_1024();
 

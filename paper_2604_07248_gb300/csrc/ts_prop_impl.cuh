@@ -544,8 +544,8 @@ template <int N>
 cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st)
 {
     if constexpr (N == 1024) {
-        if (variant == 2 && E == 32) {
-            cudaError_t e = col_pass_tma_1024(conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st);
+        if ((variant == 2 || variant == 3) && E == 32) {
+            cudaError_t e = col_pass_tma_1024(variant == 2 ? 8 : 4, conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st);
             if (e != cudaErrorNotSupported) return e;
         }
         if (variant == 1 && E == 32) {

@@ -2,10 +2,11 @@
 // Tensor Memory Accelerator while the current one is transformed (Eq. 1: column pass FFT -> H -> IFFT,
 // row pass IFFT -> exp(i phi) -> FFT).
 //
-// Column pass: a CTA of 256 threads owns 8-column tiles (64 KiB: 1024 rows x 64 bytes).  Tile k+1 is
-// loaded by four 2-D tensor copies (boxes of 256 rows x 16 floats) into the CTA's exchange buffer as
-// soon as the last exchange of tile k has been read, so the load runs under the last radix-32 stage
-// and the stores of tile k.  Thread (t, c) = (tid / 8, tid % 8) holds points t + 32 i of column c.
+// Column pass: a CTA of 32 W threads owns W-column tiles (W = 8: 64 KiB, 1024 rows x 64 bytes; or
+// W = 4).  Tile k+1 is loaded by four 2-D tensor copies (boxes of 256 rows x 2W floats) into the CTA's
+// exchange buffer as soon as the last exchange of tile k has been read, so the load runs under the
+// last radix-32 stage and the stores of tile k.  Thread (t, c) = (tid / W, tid % W) holds points
+// t + 32 i of column c.
 //
 // Row pass: every warp owns one 1024-point row at a time and its own 8 KiB line buffer, with its own
 // mbarrier: the phasor row of the step is bulk-copied into the line buffer while the second stage of
@@ -33,41 +34,51 @@ constexpr int kErrTmaWait = 4;  // error word value: a prefetch wait ran out of 
 // ---------------------------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------------------------
+// W columns per CTA (32 W threads): W = 8, two CTAs per SM, the (P, ky^2) table as float4; or W = 4,
+// four CTAs per SM (block barriers span 4 warps instead of 8), the table split into P (float2) and
+// ky^2 (float) so that four CTAs fit the SM's shared memory
+template <int W_>
 struct ColTma {
     using C = FftCfg<kN, 32>;  // 32 threads per column, 32 points each, stages 32 x 32
-    static constexpr int W = 8, THREADS = 256, BOX_ROWS = 256;
+    static constexpr int W = W_, THREADS = 32 * W, PER_SM = 16 / W, BOX_ROWS = 256;
+    static constexpr bool SPLIT = W < 8;
     static constexpr int TPF = kN / W;                       // tiles per field
-    static constexpr int LS = C::padded + 2;                 // column stride of the exchange buffer
-    static constexpr int TILE_BYTES = W * kN * 8;            // 64 KiB
+    static constexpr int LS = C::padded + (16 / W > 1 ? 16 / W : 1);  // column stride of the exchange buffer
+    static constexpr int TILE_BYTES = W * kN * 8;
     static constexpr size_t off_ht = sizeof(float2) * C::tw_smem;
-    static constexpr size_t off_buf = off_ht + sizeof(float4) * kN;
+    static constexpr size_t ht_bytes = SPLIT ? (sizeof(float2) + sizeof(float)) * kN : sizeof(float4) * kN;
+    static constexpr size_t off_buf = off_ht + ht_bytes;
     static constexpr size_t off_bar = off_buf + sizeof(float2) * W * LS;
     static constexpr size_t smem = off_bar + 16;
     static_assert(W * LS >= W * kN, "the dense tile fits the exchange buffer");
     static_assert(off_buf % 128 == 0, "TMA destination alignment");
+    static_assert(PER_SM * (smem + 1024) <= 228 * 1024, "resident CTAs fit the SM's shared memory");
 };
 
-template <bool CONJ, int HMODE>
-__global__ void __launch_bounds__(ColTma::THREADS, 2)
+template <bool CONJ, int HMODE, int W>
+__global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
     col_pass_tma_kernel(const ColParams a, const __grid_constant__ CUtensorMap tmap, int B)
 {
-    using C = ColTma::C;
-    constexpr int W = ColTma::W, TPF = ColTma::TPF;
+    using CT = ColTma<W>;
+    using C = typename CT::C;
+    constexpr int TPF = CT::TPF;
     extern __shared__ __align__(128) unsigned char sm[];
     float2* tw = reinterpret_cast<float2*>(sm);
-    float4* ht = reinterpret_cast<float4*>(sm + ColTma::off_ht);
-    float2* buf = reinterpret_cast<float2*>(sm + ColTma::off_buf);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + ColTma::off_bar);
+    float4* ht = reinterpret_cast<float4*>(sm + CT::off_ht);  // W = 8
+    float2* hp = reinterpret_cast<float2*>(sm + CT::off_ht);  // W = 4: P, then ky^2
+    float* hk = reinterpret_cast<float*>(sm + CT::off_ht + sizeof(float2) * kN);
+    float2* buf = reinterpret_cast<float2*>(sm + CT::off_buf);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + CT::off_bar);
     const int tid = threadIdx.x, c = tid % W, t = tid / W;
     const int tiles = B * TPF;
     int tile = blockIdx.x;
     if (tile >= tiles) return;  // uniform over the CTA
-    auto issue = [&](int tl) {  // one thread: the four boxes of tile tl
+    auto issue = [&](int tl) {  // one thread: the boxes of tile tl
         const int b = tl / TPF, x = 2 * (tl % TPF) * W;
-        mbar_expect_tx(bar, ColTma::TILE_BYTES);
+        mbar_expect_tx(bar, CT::TILE_BYTES);
 #pragma unroll
-        for (int q = 0; q < kN / ColTma::BOX_ROWS; ++q)
-            tma_load_2d(buf + q * ColTma::BOX_ROWS * W, &tmap, x, b * kN + q * ColTma::BOX_ROWS, bar);
+        for (int q = 0; q < kN / CT::BOX_ROWS; ++q)
+            tma_load_2d(buf + q * CT::BOX_ROWS * W, &tmap, x, b * kN + q * CT::BOX_ROWS, bar);
     };
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -75,10 +86,15 @@ __global__ void __launch_bounds__(ColTma::THREADS, 2)
         if (!a.stall) issue(tile);
     }
     stage_twiddles_c<C>(tw, a.tw);
-    for (int i = tid; i < kN; i += ColTma::THREADS) {
+    for (int i = tid; i < kN; i += CT::THREADS) {
         const float2 p = __ldg(a.P + i);
         const float k = a.dk * (float)kidx(i, kN);
-        ht[i] = make_float4(p.x, p.y, k * k, 0.0f);
+        if constexpr (CT::SPLIT) {
+            hp[i] = p;
+            hk[i] = k * k;
+        } else {
+            ht[i] = make_float4(p.x, p.y, k * k, 0.0f);
+        }
     }
     __syncthreads();
     uint32_t parity = 0;
@@ -97,10 +113,16 @@ __global__ void __launch_bounds__(ColTma::THREADS, 2)
             }
             return;
         }
-        float2* line = buf + c * ColTma::LS;
+        float2* line = buf + c * CT::LS;
         fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
         fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
-        transfer_tile<CONJ, HMODE>(v, ht, col, t, a.ccross, a.dcoef, a.inv_k2);
+        if constexpr (CT::SPLIT) {
+            transfer_tile_tab<CONJ, HMODE>(
+                v, [hp, hk](int m) { const float2 q = hp[m]; return make_float4(q.x, q.y, hk[m], 0.0f); }, col, t,
+                a.ccross, a.dcoef, a.inv_k2);
+        } else {
+            transfer_tile<CONJ, HMODE>(v, ht, col, t, a.ccross, a.dcoef, a.inv_k2);
+        }
         fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
         if (tid == 0 && tile + (int)gridDim.x < tiles) {
             fence_proxy_async();
@@ -244,26 +266,27 @@ int max_ctas(K kernel, int threads, size_t smem)
 }
 
 
-template <bool CONJ, int HMODE>
+template <bool CONJ, int HMODE, int W>
 cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
 {
+    using CT = ColTma<W>;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)2 * kN, (cuuint64_t)B * kN};
     const cuuint64_t strides[1] = {(cuuint64_t)2 * kN * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * ColTma::W), (cuuint32_t)ColTma::BOX_ROWS};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * W), (cuuint32_t)CT::BOX_ROWS};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, cp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     static int resident = 0;
-    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE>, ColTma::THREADS, ColTma::smem);
+    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, W>, CT::THREADS, CT::smem);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
-    // full residency, tiles strided over the CTAs: the two CTAs an SM holds share its issue slots, so
+    // full residency, tiles strided over the CTAs: the CTAs an SM holds share its issue slots, so
     // filling every slot keeps each SM's tile count within one of the mean
-    const int grid = std::min(B * ColTma::TPF, resident);
-    col_pass_tma_kernel<CONJ, HMODE><<<grid, ColTma::THREADS, ColTma::smem, st>>>(cp, map, B);
+    const int grid = std::min(B * CT::TPF, resident);
+    col_pass_tma_kernel<CONJ, HMODE, W><<<grid, CT::THREADS, CT::smem, st>>>(cp, map, B);
     return cudaGetLastError();
 }
 
@@ -288,16 +311,24 @@ cudaError_t tma_attr(K kernel, size_t bytes)
 
 }  // namespace
 
-cudaError_t col_pass_tma_1024(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_pass_tma_1024(int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
 {
-    if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr) return cudaErrorNotSupported;
-    switch (hmode * 2 + (conj ? 1 : 0)) {
-    case 0: return col_launch_tma<false, 0>(cp, B, st);
-    case 1: return col_launch_tma<true, 0>(cp, B, st);
-    case 2: return col_launch_tma<false, 1>(cp, B, st);
-    case 3: return col_launch_tma<true, 1>(cp, B, st);
-    case 4: return col_launch_tma<false, 2>(cp, B, st);
-    case 5: return col_launch_tma<true, 2>(cp, B, st);
+    if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr || (w != 8 && w != 4))
+        return cudaErrorNotSupported;
+    const int k = (hmode * 2 + (conj ? 1 : 0)) * 2 + (w == 4 ? 1 : 0);
+    switch (k) {
+    case 0: return col_launch_tma<false, 0, 8>(cp, B, st);
+    case 1: return col_launch_tma<false, 0, 4>(cp, B, st);
+    case 2: return col_launch_tma<true, 0, 8>(cp, B, st);
+    case 3: return col_launch_tma<true, 0, 4>(cp, B, st);
+    case 4: return col_launch_tma<false, 1, 8>(cp, B, st);
+    case 5: return col_launch_tma<false, 1, 4>(cp, B, st);
+    case 6: return col_launch_tma<true, 1, 8>(cp, B, st);
+    case 7: return col_launch_tma<true, 1, 4>(cp, B, st);
+    case 8: return col_launch_tma<false, 2, 8>(cp, B, st);
+    case 9: return col_launch_tma<false, 2, 4>(cp, B, st);
+    case 10: return col_launch_tma<true, 2, 8>(cp, B, st);
+    case 11: return col_launch_tma<true, 2, 4>(cp, B, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -321,12 +352,18 @@ cudaError_t prepare_prop_tma_1024()
     auto chk = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
-    chk(tma_attr(col_pass_tma_kernel<false, 0>, ColTma::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 0>, ColTma::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 1>, ColTma::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 1>, ColTma::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 2>, ColTma::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 2>, ColTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 0, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 0, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 1, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 1, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 2, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 2, 8>, ColTma<8>::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 0, 4>, ColTma<4>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 0, 4>, ColTma<4>::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 1, 4>, ColTma<4>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 1, 4>, ColTma<4>::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 2, 4>, ColTma<4>::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 2, 4>, ColTma<4>::smem));
     chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>, RowTma::smem));
     chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_STORE>, RowTma::smem));
     return e;

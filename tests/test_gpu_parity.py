@@ -152,7 +152,7 @@ def test_phasor_screens_give_the_same_fields_as_float_screens():
     assert np.linalg.norm(G1 - G2) / np.linalg.norm(G1) < 1e-6
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_exact_transfer_function_at_1024_both_column_variants(variant, monkeypatch):
     # dx = 0.1 mm, dz = 2 m at N = 1024: the exact transfer function in every column-pass variant
     monkeypatch.setenv("TS_FFT_E", "32")
@@ -350,17 +350,18 @@ def test_large_grid_2048_and_energy():
     assert rel_l2(U[0].cpu().numpy(), ref) < TOL
 
 
-@pytest.mark.parametrize("E,variant", [(16, 0), (32, 0), (32, 1), (32, 2)])
+@pytest.mark.parametrize("E,variant", [(16, 0), (32, 0), (32, 1), (32, 2), (32, 3)])
 def test_both_fft_variants_match_oracle(E, variant, monkeypatch):
     # the autotuner picks 16 or 32 points per thread and, at 32, the column-pass variant (lines shared
     # by four warps, one warp per column with the tile staged in shared memory, or persistent CTAs with
     # TMA-prefetched tiles); every candidate must agree with the oracle, forward and adjoint
+    rowv = 2 if variant == 3 else 0  # the 4-column tiles are a candidate with the prefetching row pass
     monkeypatch.setenv("TS_FFT_E", str(E))
     monkeypatch.setenv("TS_COL_VARIANT", str(variant))
-    monkeypatch.setenv("TS_ROW_VARIANT", "0")
+    monkeypatch.setenv("TS_ROW_VARIANT", str(rowv))
     N, dx, S = 1024, 5e-4, 3
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=2)
-    assert plan.tuning()[0] == E and plan.tuning()[5] == variant and plan.tuning()[7] == 0
+    assert plan.tuning()[0] == E and plan.tuning()[5] == variant and plan.tuning()[7] == rowv
     plan.set_sources([0.01, 0.02])
     U = cfield(2, N)
     plan.propagate(U, 2, flags=ts.TS_PROP_SOURCE, seed=4)
@@ -412,14 +413,14 @@ def test_shared_phasor_row_pass_matches_oracle(B, phi_group, monkeypatch):
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
-@pytest.mark.parametrize("B,phi_group", [(4, 2), (8, 8), (3, 3), (1, 1)])
-def test_prefetching_passes_match_oracle(B, phi_group, monkeypatch):
+@pytest.mark.parametrize("B,phi_group,colv", [(4, 2, 2), (8, 8, 2), (3, 3, 2), (1, 1, 2), (4, 2, 3), (3, 3, 3)])
+def test_prefetching_passes_match_oracle(B, phi_group, colv, monkeypatch):
     # column variant 2 (persistent CTAs, next 8-column tile by TMA) and row variant 2 (persistent warps,
     # next row and the phasor row by bulk copies), N = 1024, separable transfer function with a tiny
     # cross term: forward to the field (the last row pass also prefetches), forward to the intensity,
-    # and the adjoint; ragged persistent grids (B = 3, 1)
+    # and the adjoint; ragged persistent grids (B = 3, 1); 8-column (variant 2) and 4-column (3) tiles
     monkeypatch.setenv("TS_FFT_E", "32")
-    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_COL_VARIANT", str(colv))
     monkeypatch.setenv("TS_ROW_VARIANT", "2")
     monkeypatch.setenv("TS_PROP_STREAMS", "1")
     N, dx, S = 1024, 5e-4, 3
@@ -427,7 +428,7 @@ def test_prefetching_passes_match_oracle(B, phi_group, monkeypatch):
     md = omedium(N, dx)
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
     tune = plan.tuning()
-    assert tune[0] == 32 and tune[5] == 2 and tune[7] == 2
+    assert tune[0] == 32 and tune[5] == colv and tune[7] == 2
     phis = np.stack([np.stack([O.make_screen(md, 1e-14, 62.5, 0, 50, s, g) for s in range(S)]) for g in range(G)])
     ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
     rng = np.random.default_rng(51)
@@ -608,7 +609,7 @@ def test_tuning_candidate_table():
     plan = ts.Plan(LAM, N, dx, [62.5] * S, [1e-15] * S, l0=5e-3, L0=10.0, max_batch=4)
     cands = plan.tuning_candidates()
     assert [(e, cv, rv) for e, cv, rv, _ in cands] == [(16, 0, 0), (32, 0, 0), (32, 1, 0), (32, 0, 1), (32, 2, 0),
-                                                      (32, 0, 2), (32, 2, 2)]
+                                                      (32, 0, 2), (32, 2, 2), (32, 3, 2)]
     t = plan.tuning()
     chosen = [c for c in cands if (c[0], c[1], c[2]) == (t[0], t[5], t[7])]
     assert len(chosen) == 1
