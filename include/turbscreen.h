@@ -151,7 +151,8 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
  * row_variant[c] (0: each CTA
  * reads its screen rows; 1: phasor rows shared by the CTA's fields; 2: persistent warps that prefetch
  * their next field row and the screen phasor row with bulk asynchronous copies) and us[c], the timed
- * cost in microseconds of one column + one row pass (0 = not timed).  Variants 1 to 3 exist for
+ * cost in microseconds of one column + one row pass (0 = not timed).  Variants 2 exist for N = 512
+ * and 1024, variants 1 and 3 for
  * N = 1024 at 32 points per thread.  Output arrays may be NULL.  Host-only; no device work. */
 ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
                                     int* row_variant, float* us);

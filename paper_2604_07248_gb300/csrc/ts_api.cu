@@ -278,7 +278,8 @@ ts_status autotune(Plan& p)
         return TS_OK;
     }
     // candidates (points per thread, column variant, row variant), filtered by TS_FFT_E / TS_COL_VARIANT /
-    // TS_ROW_VARIANT; the variants other than 0 exist for N = 1024 at 32 points per thread
+    // TS_ROW_VARIANT; the variants other than 0 exist at 32 points per thread, for N = 1024 (and the
+    // prefetching variants 2 for N = 512)
     int force_e = 0, force_v = -1, force_r = -1;
     if (const char* env = std::getenv("TS_FFT_E")) force_e = std::atoi(env);
     if (const char* env = std::getenv("TS_COL_VARIANT")) force_v = std::atoi(env);
@@ -288,8 +289,12 @@ ts_status autotune(Plan& p)
     bool use[kCand];
     int n_use = 0, only = -1;
     for (int c = 0; c < kCand; ++c) {
+        // column variants 1 and 3 and row variant 1 exist for N = 1024, the prefetching variants 2
+        // for N = 512 and 1024
+        const bool avail_v = cand_v[c] == 0 || p.N == 1024 || (cand_v[c] == 2 && p.N == 512);
+        const bool avail_r = cand_r[c] == 0 || p.N == 1024 || (cand_r[c] == 2 && p.N == 512);
         use[c] = (force_e == 0 || force_e == cand_e[c]) && (force_v < 0 || force_v == cand_v[c]) &&
-                 (force_r < 0 || force_r == cand_r[c]) && ((cand_v[c] == 0 && cand_r[c] == 0) || p.N == 1024);
+                 (force_r < 0 || force_r == cand_r[c]) && avail_v && avail_r;
         if (use[c]) {
             ++n_use;
             only = c;

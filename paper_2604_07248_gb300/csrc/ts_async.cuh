@@ -79,11 +79,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// v[i] (frequency m = t + 32 i of column col) *= H or conj(H), with tab(m) = (P(m), ky(m)^2, -) read
+// v[i] (frequency m = t + T i of column col) *= H or conj(H), with tab(m) = (P(m), ky(m)^2, -) read
 // from the caller's shared-memory table (whatever its layout).  HMODE 0: exact angular-spectrum phase
 // beyond its paraxial part; 1: separable P' with the cross term exp(-i e) as a short series;
 // 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
-template <bool CONJ, int HMODE, class Tab>
+template <bool CONJ, int HMODE, class Tab, int T = 32>
 __device__ __forceinline__ void transfer_tile_tab(float2 (&v)[32], Tab tab, int col, int t, float ccross,
                                                   float dcoef, float inv_k2)
 {
@@ -93,7 +93,7 @@ __device__ __forceinline__ void transfer_tile_tab(float2 (&v)[32], Tab tab, int 
     const float cx = ccross * kx2;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        const float4 hy = tab(t + 32 * i);
+        const float4 hy = tab(t + T * i);
         const float2 q = cmul(px, make_float2(hy.x, hy.y));
         float2 h;
         if constexpr (HMODE == 0) {

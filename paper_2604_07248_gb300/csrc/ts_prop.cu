@@ -90,9 +90,9 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
 
 cudaError_t prepare_prop_kernels(int N)
 {
-    if (N == 1024) {
-        cudaError_t e = prepare_prop_tma_1024();
-        if (e == cudaSuccess) e = prepare_prop_fused_1024();
+    if (N == 512 || N == 1024) {
+        cudaError_t e = prepare_prop_tma(N);
+        if (e == cudaSuccess && N == 1024) e = prepare_prop_fused_1024();
         if (e != cudaSuccess) return e;
     }
     switch (N) {

@@ -42,13 +42,14 @@ struct ColParams {
 // Per-N entry points, instantiated in ts_prop_n<N>.cu (one translation unit per N builds in parallel).
 // variant 0: each CTA reads its own screen rows; variant 1 (N = 1024, E = 32, phasor screens): the
 // CTA's fields share one screen set and its phasor rows are staged once in shared memory; variant 2
-// (N = 1024, E = 32, phasor screens): persistent warps that prefetch their next row and the screen
-// phasor row with bulk asynchronous copies
+// (N = 512 / 1024, E = 32, phasor screens): persistent warps that prefetch their next rows and the
+// screen phasor rows with bulk asynchronous copies
 template <int N>
 cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B, cudaStream_t st);
 // variant 0: column lines shared by several warps (block synchronisation); variant 1 (N = 1024,
-// E = 32): one warp per column, tile staged through shared memory; variant 2 / 3 (N = 1024, E = 32):
-// persistent CTAs whose next 8- / 4-column tile arrives by TMA while the current one is transformed
+// E = 32): one warp per column, tile staged through shared memory; variant 2 (N = 512 / 1024, E = 32)
+// and 3 (N = 1024, E = 32): persistent CTAs whose next 64 KiB / 32 KiB tile arrives by TMA while the
+// current one is transformed
 template <int N>
 cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st);
 template <int N>
@@ -84,10 +85,11 @@ cudaError_t prepare_prop_fused_1024();
 // ht[s][m] = (P[s][m], (dk kidx(m))^2) for N = 1024
 cudaError_t build_ht_table(float4* ht, const float2* P, int S, double dk, cudaStream_t st);
 
-// the TMA-prefetching passes (ts_prop_tma.cu); cudaErrorNotSupported when the arguments do not fit them
-// w = columns per CTA (8: two CTAs per SM, 4: four CTAs per SM)
-cudaError_t col_pass_tma_1024(int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
-cudaError_t row_pass_tma_1024(int flags, const RowParams& rp, int B, cudaStream_t st);
-cudaError_t prepare_prop_tma_1024();
+// the TMA-prefetching passes (ts_prop_tma.cu), N = 512 and 1024 at 32 points per thread;
+// cudaErrorNotSupported when the arguments do not fit them.  w = columns per CTA (N = 1024: 8, two
+// CTAs per SM, or 4, four per SM; N = 512: 16)
+cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
+cudaError_t row_pass_tma(int N, int flags, const RowParams& rp, int B, cudaStream_t st);
+cudaError_t prepare_prop_tma(int N);
 
 }  // namespace ts

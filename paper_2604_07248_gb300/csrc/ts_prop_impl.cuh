@@ -513,12 +513,14 @@ cudaError_t prepare_prop_for()
 template <int N>
 cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B, cudaStream_t st)
 {
-    if constexpr (N == 1024) {
+    if constexpr (N == 512 || N == 1024) {
         // persistent warps with bulk-copy prefetch (middle and last row passes of a phasor path)
         if (variant == 2 && E == 32) {
-            cudaError_t e = row_pass_tma_1024(flags, rp, B, st);
+            cudaError_t e = row_pass_tma(N, flags, rp, B, st);
             if (e != cudaErrorNotSupported) return e;
         }
+    }
+    if constexpr (N == 1024) {
         // shared phasor rows: FPC consecutive fields of one screen set per CTA
         // (the phasor rows are staged with 16-byte loads: only for 16-byte aligned phasor arrays)
         if (variant == 1 && E == 32 && (flags & RP_PHASOR) && (reinterpret_cast<uintptr_t>(rp.phasor) & 15) == 0 &&
@@ -543,11 +545,14 @@ cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B
 template <int N>
 cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st)
 {
-    if constexpr (N == 1024) {
+    if constexpr (N == 512 || N == 1024) {
         if ((variant == 2 || variant == 3) && E == 32) {
-            cudaError_t e = col_pass_tma_1024(variant == 2 ? 8 : 4, conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st);
+            const int w = N == 512 ? 16 : (variant == 2 ? 8 : 4);
+            cudaError_t e = col_pass_tma(N, w, conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st);
             if (e != cudaErrorNotSupported) return e;
         }
+    }
+    if constexpr (N == 1024) {
         if (variant == 1 && E == 32) {
             if (sep) return conj ? col_launch_warp<N, true, true>(cp, B, st) : col_launch_warp<N, false, true>(cp, B, st);
             return conj ? col_launch_warp<N, true, false>(cp, B, st) : col_launch_warp<N, false, false>(cp, B, st);

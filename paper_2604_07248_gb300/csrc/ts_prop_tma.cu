@@ -1,17 +1,19 @@
-// ts_prop_tma.cu -- persistent propagation passes for N = 1024 that prefetch their next input with the
-// Tensor Memory Accelerator while the current one is transformed (Eq. 1: column pass FFT -> H -> IFFT,
-// row pass IFFT -> exp(i phi) -> FFT).
+// ts_prop_tma.cu -- persistent propagation passes for N = 512 and 1024 that prefetch their next input
+// with the Tensor Memory Accelerator while the current one is transformed (Eq. 1: column pass
+// FFT -> H -> IFFT, row pass IFFT -> exp(i phi) -> FFT).  32 points per thread, T = N / 32 threads per
+// line.
 //
-// Column pass: a CTA of 32 W threads owns W-column tiles (W = 8: 64 KiB, 1024 rows x 64 bytes; or
-// W = 4).  Tile k+1 is loaded by four 2-D tensor copies (boxes of 256 rows x 2W floats) into the CTA's
-// exchange buffer as soon as the last exchange of tile k has been read, so the load runs under the
-// last radix-32 stage and the stores of tile k.  Thread (t, c) = (tid / W, tid % W) holds points
-// t + 32 i of column c.
+// Column pass: a CTA of T W threads owns W-column tiles of 64 KiB (N = 1024: W = 8, or W = 4 with
+// 32 KiB tiles; N = 512: W = 16).  Tile k+1 is loaded by 2-D tensor copies (boxes of 256 rows x 2W
+// floats) into the CTA's exchange buffer as soon as the last exchange of tile k has been read, so the
+// load runs under the last FFT stage and the stores of tile k.  Thread (t, c) = (tid / W, tid % W)
+// holds points t + T i of column c.
 //
-// Row pass: every warp owns one 1024-point row at a time and its own 8 KiB line buffer, with its own
-// mbarrier: the phasor row of the step is bulk-copied into the line buffer while the second stage of
-// the inverse FFT runs, and the warp's next field row while the second stage of the forward FFT runs.
-// Warps never wait for one another after the twiddles are staged.
+// Row pass: every warp owns 32 / T consecutive rows at a time (one at N = 1024, two at 512) and its
+// own 8 KiB of line buffers, with its own mbarrier: the phasor rows of the step are bulk-copied into
+// the lines while the second stage of the inverse FFT runs, and the warp's next field rows while the
+// second stage of the forward FFT runs.  Warps never wait for one another after the twiddles are
+// staged.
 //
 // Every wait on an mbarrier is bounded by the plan's clock64 budget; a wait that runs out sets the
 // plan's error word (read by ts_plan_device_status) and the CTA (column pass) or warp (row pass)
@@ -28,45 +30,45 @@ namespace ts {
 namespace {
 
 using namespace async;
-constexpr int kN = 1024;
 constexpr int kErrTmaWait = 4;  // error word value: a prefetch wait ran out of its budget
 
 // ---------------------------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------------------------
-// W columns per CTA (32 W threads): W = 8, two CTAs per SM, the (P, ky^2) table as float4; or W = 4,
-// four CTAs per SM (block barriers span 4 warps instead of 8), the table split into P (float2) and
-// ky^2 (float) so that four CTAs fit the SM's shared memory
-template <int W_>
+// W columns per CTA (T W threads): N = 1024, W = 8, two CTAs per SM, the (P, ky^2) table as float4;
+// or W = 4, four CTAs per SM (block barriers span 4 warps instead of 8), the table split into P
+// (float2) and ky^2 (float) so that four CTAs fit the SM's shared memory; N = 512, W = 16, two per SM.
+template <int N_, int W_>
 struct ColTma {
-    using C = FftCfg<kN, 32>;  // 32 threads per column, 32 points each, stages 32 x 32
-    static constexpr int W = W_, THREADS = 32 * W, PER_SM = 16 / W, BOX_ROWS = 256;
-    static constexpr bool SPLIT = W < 8;
-    static constexpr int TPF = kN / W;                       // tiles per field
+    static constexpr int N = N_, W = W_;
+    using C = FftCfg<N, 32>;  // T = N / 32 threads per column, 32 points each
+    static constexpr int T = C::T, THREADS = T * W, PER_SM = 512 / THREADS, BOX_ROWS = 256;
+    static constexpr bool SPLIT = PER_SM > 2;
+    static constexpr int TPF = N / W;                        // tiles per field
     static constexpr int LS = C::padded + (16 / W > 1 ? 16 / W : 1);  // column stride of the exchange buffer
-    static constexpr int TILE_BYTES = W * kN * 8;
+    static constexpr int TILE_BYTES = W * N * 8;
     static constexpr size_t off_ht = sizeof(float2) * C::tw_smem;
-    static constexpr size_t ht_bytes = SPLIT ? (sizeof(float2) + sizeof(float)) * kN : sizeof(float4) * kN;
+    static constexpr size_t ht_bytes = SPLIT ? (sizeof(float2) + sizeof(float)) * N : sizeof(float4) * N;
     static constexpr size_t off_buf = off_ht + ht_bytes;
     static constexpr size_t off_bar = off_buf + sizeof(float2) * W * LS;
     static constexpr size_t smem = off_bar + 16;
-    static_assert(W * LS >= W * kN, "the dense tile fits the exchange buffer");
+    static_assert(W * LS >= W * N, "the dense tile fits the exchange buffer");
     static_assert(off_buf % 128 == 0, "TMA destination alignment");
+    static_assert(N % BOX_ROWS == 0 && (2 * W * 4) % 16 == 0, "whole boxes, 16-byte box rows");
     static_assert(PER_SM * (smem + 1024) <= 228 * 1024, "resident CTAs fit the SM's shared memory");
 };
 
-template <bool CONJ, int HMODE, int W>
-__global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
+template <bool CONJ, int HMODE, class CT>
+__global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
     col_pass_tma_kernel(const ColParams a, const __grid_constant__ CUtensorMap tmap, int B)
 {
-    using CT = ColTma<W>;
     using C = typename CT::C;
-    constexpr int TPF = CT::TPF;
+    constexpr int N = CT::N, W = CT::W, T = CT::T, TPF = CT::TPF;
     extern __shared__ __align__(128) unsigned char sm[];
     float2* tw = reinterpret_cast<float2*>(sm);
-    float4* ht = reinterpret_cast<float4*>(sm + CT::off_ht);  // W = 8
-    float2* hp = reinterpret_cast<float2*>(sm + CT::off_ht);  // W = 4: P, then ky^2
-    float* hk = reinterpret_cast<float*>(sm + CT::off_ht + sizeof(float2) * kN);
+    float4* ht = reinterpret_cast<float4*>(sm + CT::off_ht);  // float4 table
+    float2* hp = reinterpret_cast<float2*>(sm + CT::off_ht);  // split table: P, then ky^2
+    float* hk = reinterpret_cast<float*>(sm + CT::off_ht + sizeof(float2) * N);
     float2* buf = reinterpret_cast<float2*>(sm + CT::off_buf);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + CT::off_bar);
     const int tid = threadIdx.x, c = tid % W, t = tid / W;
@@ -77,8 +79,8 @@ __global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
         const int b = tl / TPF, x = 2 * (tl % TPF) * W;
         mbar_expect_tx(bar, CT::TILE_BYTES);
 #pragma unroll
-        for (int q = 0; q < kN / CT::BOX_ROWS; ++q)
-            tma_load_2d(buf + q * CT::BOX_ROWS * W, &tmap, x, b * kN + q * CT::BOX_ROWS, bar);
+        for (int q = 0; q < N / CT::BOX_ROWS; ++q)
+            tma_load_2d(buf + q * CT::BOX_ROWS * W, &tmap, x, b * N + q * CT::BOX_ROWS, bar);
     };
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -86,9 +88,9 @@ __global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
         if (!a.stall) issue(tile);
     }
     stage_twiddles_c<C>(tw, a.tw);
-    for (int i = tid; i < kN; i += CT::THREADS) {
+    for (int i = tid; i < N; i += CT::THREADS) {
         const float2 p = __ldg(a.P + i);
-        const float k = a.dk * (float)kidx(i, kN);
+        const float k = a.dk * (float)kidx(i, N);
         if constexpr (CT::SPLIT) {
             hp[i] = p;
             hk[i] = k * k;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
         float2 v[32];
         if (ok) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = buf[(t + 32 * i) * W + c];
+            for (int i = 0; i < 32; ++i) v[i] = buf[(t + T * i) * W + c];
         }
         if (__syncthreads_or(!ok)) {  // every thread has read the tile before the exchange reuses it
             if (tid == 0) {
@@ -117,11 +119,14 @@ __global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
         fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
         fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
         if constexpr (CT::SPLIT) {
-            transfer_tile_tab<CONJ, HMODE>(
-                v, [hp, hk](int m) { const float2 q = hp[m]; return make_float4(q.x, q.y, hk[m], 0.0f); }, col, t,
-                a.ccross, a.dcoef, a.inv_k2);
+            auto tab = [hp, hk](int m) {
+                const float2 q = hp[m];
+                return make_float4(q.x, q.y, hk[m], 0.0f);
+            };
+            transfer_tile_tab<CONJ, HMODE, decltype(tab), T>(v, tab, col, t, a.ccross, a.dcoef, a.inv_k2);
         } else {
-            transfer_tile<CONJ, HMODE>(v, ht, col, t, a.ccross, a.dcoef, a.inv_k2);
+            auto tab = [ht](int m) { return ht[m]; };
+            transfer_tile_tab<CONJ, HMODE, decltype(tab), T>(v, tab, col, t, a.ccross, a.dcoef, a.inv_k2);
         }
         fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
         if (tid == 0 && tile + (int)gridDim.x < tiles) {
@@ -129,54 +134,64 @@ __global__ void __launch_bounds__(ColTma<W>::THREADS, ColTma<W>::PER_SM)
             issue(tile + gridDim.x);
         }
         fft_stage_c<C, 1, +1>(v, line, t, tw, BlockBar());
-        float2* base = a.field + (size_t)b * kN * kN + col;
+        float2* base = a.field + (size_t)b * N * N + col;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) base[(size_t)(t + 32 * i) * kN] = v[i];
+        for (int i = 0; i < 32; ++i) base[(size_t)(t + T * i) * N] = v[i];
     }
 }
 
 // ---------------------------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------------------------
+template <int N_>
 struct RowTma {
-    using C = FftCfg<kN, 32>;  // one warp per row
+    static constexpr int N = N_;
+    using C = FftCfg<N, 32>;  // T = N / 32 threads per row, 32 / T rows per warp
+    static constexpr int T = C::T, RPW = 32 / T;
     static constexpr int WARPS = 8, THREADS = 32 * WARPS;
     static constexpr int LS = C::padded;  // line stride (float2); a line holds the dense row or the exchange
-    static constexpr int ROW_BYTES = kN * 8;
+    static constexpr int ROW_BYTES = N * 8;
     static constexpr size_t off_line = sizeof(float2) * C::tw_smem;
-    static constexpr size_t off_bar = off_line + sizeof(float2) * WARPS * LS;
+    static constexpr size_t off_bar = off_line + sizeof(float2) * WARPS * RPW * LS;
     static constexpr size_t smem = off_bar + 8 * WARPS;
+    static_assert(T <= 32 && 32 % T == 0, "whole rows per warp");
     static_assert(off_line % 128 == 0 && (sizeof(float2) * LS) % 16 == 0, "bulk-copy destination alignment");
 };
 
-template <int FLAGS>
-__global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const RowParams a, int B)
+template <class RT, int FLAGS>
+__global__ void __launch_bounds__(RT::THREADS, 2) row_pass_tma_kernel(const RowParams a, int B)
 {
-    using C = RowTma::C;
+    using C = typename RT::C;
+    constexpr int N = RT::N, T = RT::T, RPW = RT::RPW;
     static_assert((FLAGS & RP_IN_FREQ) && (FLAGS & RP_PHASOR) && (FLAGS & RP_STORE) && !(FLAGS & RP_INTENSITY) &&
                       !(FLAGS & RP_IN_SOURCE),
                   "row pass of a step in the row-frequency domain");
     extern __shared__ __align__(128) unsigned char sm[];
     float2* tw = reinterpret_cast<float2*>(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* line = reinterpret_cast<float2*>(sm + RowTma::off_line) + warp * RowTma::LS;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RowTma::off_bar) + warp;
-    const int rows = B * kN;
-    // rows gw, gw + stride, ... of the launch (strided over every warp of the grid)
-    const int gw = blockIdx.x * RowTma::WARPS + warp, stride = gridDim.x * RowTma::WARPS;
+    const int h = lane / T, t = lane % T;  // this lane's row of the warp's RPW rows, and its thread index in it
+    float2* lines = reinterpret_cast<float2*>(sm + RT::off_line) + warp * RPW * RT::LS;
+    float2* line = lines + h * RT::LS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + RT::off_bar) + warp;
+    const int units = B * N / RPW;  // groups of RPW consecutive rows (never across fields)
+    // units gw, gw + stride, ... of the launch (strided over every warp of the grid)
+    const int gw = blockIdx.x * RT::WARPS + warp, stride = gridDim.x * RT::WARPS;
+    auto load_rows = [&](int u) {  // lane 0: the RPW field rows of unit u
+        mbar_expect_tx(bar, RPW * RT::ROW_BYTES);
+#pragma unroll
+        for (int k = 0; k < RPW; ++k)
+            bulk_load(lines + k * RT::LS, a.field + ((size_t)u * RPW + k) * N, RT::ROW_BYTES, bar);
+    };
     if (lane == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
-        if (gw < rows && !a.stall) {
-            mbar_expect_tx(bar, RowTma::ROW_BYTES);
-            bulk_load(line, a.field + (size_t)gw * kN, RowTma::ROW_BYTES, bar);
-        }
+        if (gw < units && !a.stall) load_rows(gw);
     }
     stage_twiddles_c<C>(tw, a.tw);
     __syncthreads();
     uint32_t parity = 0;
-    for (int r = gw; r < rows; r += stride) {
-        const int b = r / kN, j = r % kN;
+    for (int u = gw; u < units; u += stride) {
+        const int r0 = u * RPW, b = r0 / N, j0 = r0 % N;
         float2 v[32];
         if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, a.budget))) {
             if (lane == 0) {
@@ -187,16 +202,18 @@ __global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const 
         }
         parity ^= 1u;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = line[lane + 32 * i];
-        __syncwarp();  // every lane has its points before the exchange overwrites the row
-        fft_stage_c<C, 0, +1>(v, line, lane, tw, WarpBar());
-        if (lane == 0) {  // the line is free: the step's screen phasor row comes in under the next stage
+        for (int i = 0; i < 32; ++i) v[i] = line[t + T * i];
+        __syncwarp();  // every lane has its points before the exchange overwrites the rows
+        fft_stage_c<C, 0, +1>(v, line, t, tw, WarpBar());
+        if (lane == 0) {  // the lines are free: the step's screen phasor rows come in under the next stage
             const int set = (b + a.phi_off) / a.phi_group;
+            const float2* src = a.phasor + (long long)set * a.phi_set_stride + (size_t)j0 * N;
             fence_proxy_async();
-            mbar_expect_tx(bar, RowTma::ROW_BYTES);
-            bulk_load(line, a.phasor + (long long)set * a.phi_set_stride + (size_t)j * kN, RowTma::ROW_BYTES, bar);
+            mbar_expect_tx(bar, RPW * RT::ROW_BYTES);
+#pragma unroll
+            for (int k = 0; k < RPW; ++k) bulk_load(lines + k * RT::LS, src + (size_t)k * N, RT::ROW_BYTES, bar);
         }
-        fft_stage_c<C, 1, +1>(v, line, lane, tw, WarpBar());
+        fft_stage_c<C, 1, +1>(v, line, t, tw, WarpBar());
         if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, a.budget))) {
             if (lane == 0) {
                 atomicExch(a.err, kErrTmaWait);
@@ -207,30 +224,28 @@ __global__ void __launch_bounds__(RowTma::THREADS, 2) row_pass_tma_kernel(const 
         parity ^= 1u;
         if (a.phase_sign > 0.0f) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = cmul(v[i], line[lane + 32 * i]);
+            for (int i = 0; i < 32; ++i) v[i] = cmul(v[i], line[t + T * i]);
         } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = cmulc(v[i], line[lane + 32 * i]);
+            for (int i = 0; i < 32; ++i) v[i] = cmulc(v[i], line[t + T * i]);
         }
         __syncwarp();
         if constexpr (FLAGS & RP_OUT_FREQ) {
-            fft_stage_c<C, 0, -1>(v, line, lane, tw, WarpBar());
-            if (lane == 0 && r + stride < rows) {
+            fft_stage_c<C, 0, -1>(v, line, t, tw, WarpBar());
+            if (lane == 0 && u + stride < units) {
                 fence_proxy_async();
-                mbar_expect_tx(bar, RowTma::ROW_BYTES);
-                bulk_load(line, a.field + (size_t)(r + stride) * kN, RowTma::ROW_BYTES, bar);
+                load_rows(u + stride);
             }
-            fft_stage_c<C, 1, -1>(v, line, lane, tw, WarpBar());
+            fft_stage_c<C, 1, -1>(v, line, t, tw, WarpBar());
         } else {
-            if (lane == 0 && r + stride < rows) {
+            if (lane == 0 && u + stride < units) {
                 fence_proxy_async();
-                mbar_expect_tx(bar, RowTma::ROW_BYTES);
-                bulk_load(line, a.field + (size_t)(r + stride) * kN, RowTma::ROW_BYTES, bar);
+                load_rows(u + stride);
             }
         }
-        float2* row = a.field + (size_t)r * kN;
+        float2* row = a.field + ((size_t)r0 + h) * N;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) row[lane + 32 * i] = v[i];
+        for (int i = 0; i < 32; ++i) row[t + T * i] = v[i];
     }
 }
 
@@ -266,39 +281,65 @@ int max_ctas(K kernel, int threads, size_t smem)
 }
 
 
-template <bool CONJ, int HMODE, int W>
+template <bool CONJ, int HMODE, class CT>
 cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
 {
-    using CT = ColTma<W>;
+    constexpr int N = CT::N, W = CT::W;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)2 * kN, (cuuint64_t)B * kN};
-    const cuuint64_t strides[1] = {(cuuint64_t)2 * kN * sizeof(float)};
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * N, (cuuint64_t)B * N};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * N * sizeof(float)};
     const cuuint32_t box[2] = {(cuuint32_t)(2 * W), (cuuint32_t)CT::BOX_ROWS};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, cp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     static int resident = 0;
-    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, W>, CT::THREADS, CT::smem);
+    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, CT>, CT::THREADS, CT::smem);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     // full residency, tiles strided over the CTAs: the CTAs an SM holds share its issue slots, so
     // filling every slot keeps each SM's tile count within one of the mean
     const int grid = std::min(B * CT::TPF, resident);
-    col_pass_tma_kernel<CONJ, HMODE, W><<<grid, CT::THREADS, CT::smem, st>>>(cp, map, B);
+    col_pass_tma_kernel<CONJ, HMODE, CT><<<grid, CT::THREADS, CT::smem, st>>>(cp, map, B);
     return cudaGetLastError();
 }
 
-template <int FLAGS>
+template <class CT>
+cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+{
+    switch (hmode * 2 + (conj ? 1 : 0)) {
+    case 0: return col_launch_tma<false, 0, CT>(cp, B, st);
+    case 1: return col_launch_tma<true, 0, CT>(cp, B, st);
+    case 2: return col_launch_tma<false, 1, CT>(cp, B, st);
+    case 3: return col_launch_tma<true, 1, CT>(cp, B, st);
+    case 4: return col_launch_tma<false, 2, CT>(cp, B, st);
+    case 5: return col_launch_tma<true, 2, CT>(cp, B, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class RT, int FLAGS>
 cudaError_t row_launch_tma(const RowParams& rp, int B, cudaStream_t st)
 {
     static int resident = 0;
-    if (resident == 0) resident = max_ctas(row_pass_tma_kernel<FLAGS>, RowTma::THREADS, RowTma::smem);
+    if (resident == 0) resident = max_ctas(row_pass_tma_kernel<RT, FLAGS>, RT::THREADS, RT::smem);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
-    const int grid = std::min((B * kN + RowTma::WARPS - 1) / RowTma::WARPS, resident);  // full residency
-    row_pass_tma_kernel<FLAGS><<<grid, RowTma::THREADS, RowTma::smem, st>>>(rp, B);
+    const int units = B * RT::N / RT::RPW;
+    const int grid = std::min((units + RT::WARPS - 1) / RT::WARPS, resident);  // full residency
+    row_pass_tma_kernel<RT, FLAGS><<<grid, RT::THREADS, RT::smem, st>>>(rp, B);
     return cudaGetLastError();
+}
+
+template <class RT>
+cudaError_t row_dispatch_tma(int flags, const RowParams& rp, int B, cudaStream_t st)
+{
+    switch (flags) {
+    case RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE:
+        return row_launch_tma<RT, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>(rp, B, st);
+    case RP_IN_FREQ | RP_PHASOR | RP_STORE: return row_launch_tma<RT, RP_IN_FREQ | RP_PHASOR | RP_STORE>(rp, B, st);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 template <class K>
@@ -311,61 +352,58 @@ cudaError_t tma_attr(K kernel, size_t bytes)
 
 }  // namespace
 
-cudaError_t col_pass_tma_1024(int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
 {
-    if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr || (w != 8 && w != 4))
-        return cudaErrorNotSupported;
-    const int k = (hmode * 2 + (conj ? 1 : 0)) * 2 + (w == 4 ? 1 : 0);
-    switch (k) {
-    case 0: return col_launch_tma<false, 0, 8>(cp, B, st);
-    case 1: return col_launch_tma<false, 0, 4>(cp, B, st);
-    case 2: return col_launch_tma<true, 0, 8>(cp, B, st);
-    case 3: return col_launch_tma<true, 0, 4>(cp, B, st);
-    case 4: return col_launch_tma<false, 1, 8>(cp, B, st);
-    case 5: return col_launch_tma<false, 1, 4>(cp, B, st);
-    case 6: return col_launch_tma<true, 1, 8>(cp, B, st);
-    case 7: return col_launch_tma<true, 1, 4>(cp, B, st);
-    case 8: return col_launch_tma<false, 2, 8>(cp, B, st);
-    case 9: return col_launch_tma<false, 2, 4>(cp, B, st);
-    case 10: return col_launch_tma<true, 2, 8>(cp, B, st);
-    case 11: return col_launch_tma<true, 2, 4>(cp, B, st);
-    default: return cudaErrorInvalidValue;
-    }
+    if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr) return cudaErrorNotSupported;
+    if (N == 1024 && w == 8) return col_dispatch_tma<ColTma<1024, 8>>(conj, hmode, cp, B, st);
+    if (N == 1024 && w == 4) return col_dispatch_tma<ColTma<1024, 4>>(conj, hmode, cp, B, st);
+    if (N == 512 && w == 16) return col_dispatch_tma<ColTma<512, 16>>(conj, hmode, cp, B, st);
+    return cudaErrorNotSupported;
 }
 
-cudaError_t row_pass_tma_1024(int flags, const RowParams& rp, int B, cudaStream_t st)
+cudaError_t row_pass_tma(int N, int flags, const RowParams& rp, int B, cudaStream_t st)
 {
     if ((reinterpret_cast<uintptr_t>(rp.field) & 15) != 0 || (reinterpret_cast<uintptr_t>(rp.phasor) & 15) != 0 ||
         (rp.phi_set_stride & 1) != 0 || rp.err == nullptr || rp.phasor == nullptr)
         return cudaErrorNotSupported;
-    switch (flags) {
-    case RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE:
-        return row_launch_tma<RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>(rp, B, st);
-    case RP_IN_FREQ | RP_PHASOR | RP_STORE: return row_launch_tma<RP_IN_FREQ | RP_PHASOR | RP_STORE>(rp, B, st);
-    default: return cudaErrorNotSupported;
-    }
+    if (N == 1024) return row_dispatch_tma<RowTma<1024>>(flags, rp, B, st);
+    if (N == 512) return row_dispatch_tma<RowTma<512>>(flags, rp, B, st);
+    return cudaErrorNotSupported;
 }
 
-cudaError_t prepare_prop_tma_1024()
+namespace {
+template <class CT>
+void col_attrs(cudaError_t& e)
 {
-    cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
-    chk(tma_attr(col_pass_tma_kernel<false, 0, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 0, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 1, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 1, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 2, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 2, 8>, ColTma<8>::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 0, 4>, ColTma<4>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 0, 4>, ColTma<4>::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 1, 4>, ColTma<4>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 1, 4>, ColTma<4>::smem));
-    chk(tma_attr(col_pass_tma_kernel<false, 2, 4>, ColTma<4>::smem));
-    chk(tma_attr(col_pass_tma_kernel<true, 2, 4>, ColTma<4>::smem));
-    chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>, RowTma::smem));
-    chk(tma_attr(row_pass_tma_kernel<RP_IN_FREQ | RP_PHASOR | RP_STORE>, RowTma::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 0, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 0, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 1, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 1, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 2, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 2, CT>, CT::smem));
+}
+template <class RT>
+void row_attrs(cudaError_t& e)
+{
+    if (e == cudaSuccess) e = tma_attr(row_pass_tma_kernel<RT, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>, RT::smem);
+    if (e == cudaSuccess) e = tma_attr(row_pass_tma_kernel<RT, RP_IN_FREQ | RP_PHASOR | RP_STORE>, RT::smem);
+}
+}  // namespace
+
+cudaError_t prepare_prop_tma(int N)
+{
+    cudaError_t e = cudaSuccess;
+    if (N == 1024) {
+        col_attrs<ColTma<1024, 8>>(e);
+        col_attrs<ColTma<1024, 4>>(e);
+        row_attrs<RowTma<1024>>(e);
+    } else if (N == 512) {
+        col_attrs<ColTma<512, 16>>(e);
+        row_attrs<RowTma<512>>(e);
+    }
     return e;
 }
 

@@ -451,6 +451,37 @@ def test_prefetching_passes_match_oracle(B, phi_group, colv, monkeypatch):
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
+@pytest.mark.parametrize("B,phi_group", [(4, 2), (3, 3), (1, 1)])
+def test_prefetching_passes_at_512_match_oracle(B, phi_group, monkeypatch):
+    # N = 512: 16-column tiles of 64 KiB, two rows per warp in the row pass (16 threads per row)
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    monkeypatch.setenv("TS_PROP_STREAMS", "1")
+    N, dx, S = 512, 1e-3, 3
+    G = (B + phi_group - 1) // phi_group
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [100.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    tune = plan.tuning()
+    assert tune[0] == 32 and tune[5] == 2 and tune[7] == 2
+    phis = np.stack([np.stack([O.make_screen(md, 1e-14, 100.0, 0, 70, s, g) for s in range(S)]) for g in range(G)])
+    ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
+    rng = np.random.default_rng(71)
+    U0 = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    U = torch.from_numpy(U0).to(DEV)
+    plan.propagate(U, B, phasor=ph, phi_group=phi_group)
+    g = torch.from_numpy(U0).to(DEV)
+    plan.propagate_backward(g, B, phasor=ph, phi_group=phi_group)
+    plan.device_status()
+    got, gg = U.cpu().numpy(), g.cpu().numpy()
+    for b in range(B):
+        set_phi = np.angle(np.exp(1j * phis[b // phi_group]))
+        ref = O.propagate(md, [100.0] * S, set_phi, U0[b])
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+        back = O.propagate_adjoint(md, [100.0] * S, set_phi, U0[b])
+        assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
+
+
 def test_prefetching_column_pass_with_the_series_cross_term(monkeypatch):
     # dz = 2500 m at dx = 0.5 mm (above the Eq. 7 limit, so the plan allows aliasing): the cross term
     # reaches 0.015 rad, the separable transfer function applies exp(-i e) as its short series
