@@ -122,17 +122,19 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
-def algorithmic_bytes(N, B, S):
+def algorithmic_bytes(N, B, S, source_in_column=False):
     """Bytes one launch of each kernel kind must move (the roofline numerator), per the 2-pass model:
     column pass: field read + write; row passes: field read + write, screen read once (shared by the
     beams), the first pass writes only; screen synthesis: AR state read + write, column-transformed
     spectrum write + read, screen phasor write (8 B), PSD shape read once; fused propagation: the
     whole ts_propagate call (first row pass and S column + row passes, see propagate_bytes)."""
     px = N * N
-    col = 16 * B * px
+    # averages over the launches of one call: with the sources generated in the first column pass,
+    # that pass only writes and there is no first row pass
+    col = (16 * S - (8 if source_in_column else 0)) * B * px / S
     row_first = 8 * B * px
     row_mid = 16 * B * px + 8 * px
-    row_avg = (row_first + S * row_mid) / (S + 1)
+    row_avg = row_mid if source_in_column else (row_first + S * row_mid) / (S + 1)
     screens = S * 40 * px + 4 * px
     fused = propagate_bytes(N, B, S, B)  # one launch = the whole propagation of the B fields
     return {0: col, 1: row_avg, 2: screens, 3: fused}
@@ -146,16 +148,19 @@ def hbm_peak():
     return 6800.0, "fallback"
 
 
-def propagate_bytes(N, B, S, shared_screen_fields, intensity_only=False):
+def propagate_bytes(N, B, S, shared_screen_fields, intensity_only=False, source_in_column=False):
     """Algorithmic bytes of one ts_propagate call of B fields through S phasor screens, each screen
     set shared by `shared_screen_fields` fields: first row pass writes the field (8 B/px); every
     column pass reads + writes it (16); middle row passes read + write it (16) and read the phasor
     once per set (8); the last row pass reads the field and the phasor and writes the field (or
-    only the 4-byte intensity)."""
+    only the 4-byte intensity).  With the sources generated in the first column pass there is no
+    first row pass and that column pass only writes (8)."""
     px = N * N
     sets = B / shared_screen_fields
     last = (8 + 4) if intensity_only else (8 + 8)
-    return px * (8 * B + S * 16 * B + (S - 1) * 16 * B + last * B + S * 8 * sets)
+    first = 0 if source_in_column else 8 * B
+    cols = S * 16 * B - (8 * B if source_in_column else 0)
+    return px * (first + cols + (S - 1) * 16 * B + last * B + S * 8 * sets)
 
 
 def screen_bytes(N, n_screens, ar=False):
@@ -252,7 +257,8 @@ def run_gpu(args):
 
     groups = plan.tuning()[3]  # concurrent field groups chosen by the autotuner
     fused = plan.tuning_fused()  # (fused persistent launch chosen, us per-pass, us fused)
-    launches_per_step = 2 + (1 if fused[0] else groups * (1 + 2 * S))
+    src_first = plan.tuning()[5] in (2, 3) and N in (512, 1024)  # no first row pass (sources in the column pass)
+    launches_per_step = 2 + (1 if fused[0] else groups * ((0 if src_first else 1) + 2 * S))
     for _ in range(args.warmup):
         step()
     barrier()
@@ -298,7 +304,9 @@ def run_gpu(args):
     kinds = {0: "col_pass", 1: "row_pass", 2: "screen_synthesis", 3: "propagation_fused"}
     kt = {k: plan_for_timing.timing_read(k) for k in kinds}
     plan_for_timing.timing(False)
-    algo = algorithmic_bytes(N, B, S)
+    # the first column pass generates the sources when the prefetching column pass runs per-pass
+    src_col = (not fused[0]) and tune[5] in (2, 3) and N in (512, 1024)
+    algo = algorithmic_bytes(N, B, S, source_in_column=src_col)
     measured = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = float(measured["hbm_gbs"]) if measured else 6800.0
@@ -425,7 +433,7 @@ def run_gpu(args):
     h1.record(stream)
     barrier()
     ms_loop = max_over_ranks(h0.elapsed_time(h1)) / n_loop
-    loop_bytes = propagate_bytes(N, B, S, B)
+    loop_bytes = propagate_bytes(N, B, S, B, source_in_column=src_col)
     loop_gbs = loop_bytes / (ms_loop * 1e-3) / 1e9
     roof["split_step_loop"] = {"algorithmic_bytes": int(loop_bytes), "us_per_call": round(ms_loop * 1e3, 2),
                                "achieved": round(loop_gbs, 1), "frac": round(loop_gbs / peak, 4), "calls": n_loop,
@@ -434,7 +442,7 @@ def run_gpu(args):
 
     # the whole timed step against the same peak: algorithmic bytes of one step (AR update + synthesis
     # of the S screens, propagation of the B beams) / device time per step
-    step_bytes = screen_bytes(N, S, ar=True) + propagate_bytes(N, B, S, B)
+    step_bytes = screen_bytes(N, S, ar=True) + propagate_bytes(N, B, S, B, source_in_column=src_col)
     step_gbs = step_bytes / (ms / args.steps * 1e-3) / 1e9
     roof["step"] = {"algorithmic_bytes": int(step_bytes), "achieved": round(step_gbs, 1),
                     "frac": round(step_gbs / peak, 4),

@@ -93,7 +93,7 @@ void free_plan(Plan* p)
     if (p->fork) cudaEventDestroy(p->fork);
     void* ptrs[] = {p->tw,  p->P,    p->dcoef, p->amp,       p->g,         p->shx,      p->shy,    p->shy_mean,
                     p->shb, p->tilt, p->ws_y,  p->ws_shv,    p->ws_shmean, p->ws_sha,   p->ws_phi, p->ws_rows,
-                    p->tw16 != p->tw ? p->tw16 : nullptr, p->d_err, p->ht_all, p->fused_ctr};
+                    p->tw16 != p->tw ? p->tw16 : nullptr, p->d_err, p->ht_all, p->fused_ctr, p->src_fx, p->src_gy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -181,12 +181,25 @@ ts_status prop_range(Plan& p, float2* U, int b0, int B, const float* phi, const 
         set_error("");  // arguments the fused launch does not take: per-pass launches below
     }
     const int f0 = ((flags & TS_PROP_SOURCE) ? RP_IN_SOURCE : 0) | RP_OUT_FREQ | RP_STORE;
-    ts_status stt =
-        cuda_check(timed(p, 1, st, [&] { return launch_row_pass(p, f0, ra, st); }), "ts_propagate first row pass");
-    if (stt != TS_OK) return stt;
+    // With sources, the prefetching column pass generates the row transform of each source in its
+    // first step (a rank-one product), so the first row pass is not needed
+    bool src_in_col = (flags & TS_PROP_SOURCE) && p.src_fx && !p.split_bf16 && p.fft_e == 32 &&
+                      (p.col_variant == 2 || p.col_variant == 3) && (p.N == 512 || p.N == 1024) &&
+                      (reinterpret_cast<uintptr_t>(Ur) & 15) == 0;
+    ts_status stt = TS_OK;
+    if (!src_in_col) {
+        stt = cuda_check(timed(p, 1, st, [&] { return launch_row_pass(p, f0, ra, st); }), "ts_propagate first row pass");
+        if (stt != TS_OK) return stt;
+    }
     for (int s = 0; s < S; ++s) {
-        stt = cuda_check(timed(p, 0, st, [&] { return launch_col_pass(p, s, false, Ur, B, st); }),
-                         "ts_propagate column pass");
+        const bool src = src_in_col && s == 0;
+        cudaError_t ec = timed(p, 0, st, [&] { return launch_col_pass(p, s, false, Ur, B, st, src, b0); });
+        if (src && ec == cudaErrorNotSupported) {  // the kernels could not take it after all: row pass first
+            (void)cudaGetLastError();
+            ec = timed(p, 1, st, [&] { return launch_row_pass(p, f0, ra, st); });
+            if (ec == cudaSuccess) ec = timed(p, 0, st, [&] { return launch_col_pass(p, s, false, Ur, B, st); });
+        }
+        stt = cuda_check(ec, "ts_propagate column pass");
         if (stt != TS_OK) return stt;
         int rf = RP_IN_FREQ | RP_STORE;
         ra.phi = nullptr;
@@ -673,6 +686,10 @@ ts_status ts_plan_create_psd(ts_plan* out, const ts_medium* medium, const ts_gri
     p->regen_all = (size_t)max_batch * S * N2 * sizeof(float2) <= (256ull << 20);
     ok(dalloc(*p, &p->ws_phi, (size_t)max_batch * (p->regen_all ? S : 1) * N2));
     ok(dalloc(*p, &p->ws_rows, (size_t)max_batch * N * 4));
+    if ((N == 512 || N == 1024) && !p->split_bf16) {
+        ok(dalloc(*p, &p->src_fx, (size_t)kMaxSources * N));
+        ok(dalloc(*p, &p->src_gy, (size_t)kMaxSources * N));
+    }
     if (N == 1024 && !p->split_bf16) {
         ok(dalloc(*p, &p->ht_all, (size_t)S * N));
         ok(dalloc(*p, &p->fused_ctr, (size_t)(2 * S + 1) * max_batch + 1));
@@ -833,6 +850,32 @@ ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0)
     Plan* p = reinterpret_cast<Plan*>(plan);
     for (int i = 0; i < n; ++i) p->src_coef[i] = w0[i] > 0.0 ? (float)(p->dx * p->dx / (w0[i] * w0[i])) : -1.0f;
     p->n_src = n;
+    if (p->src_fx) {
+        // row DFT of each source's x profile and its y profile, FP64: the first column pass of a call
+        // with sources starts from R0(kx, y) = Fx(kx) gy(y), the row transform of the separable source
+        // U0 = exp(-(x^2 + y^2) dx^2 / w0^2) (pixel offsets from N/2; a plane wave has Fx = N delta)
+        const int N = p->N;
+        std::vector<float2> fx((size_t)n * N);
+        std::vector<float> gy((size_t)n * N);
+        std::vector<double> cs(N), g(N);
+        for (int q = 0; q < N; ++q) cs[q] = std::cos(2.0 * M_PI * q / N);
+        for (int i = 0; i < n; ++i) {
+            const double c = w0[i] > 0.0 ? p->dx * p->dx / (w0[i] * w0[i]) : -1.0;
+            for (int x = 0; x < N; ++x) g[x] = c < 0.0 ? 1.0 : std::exp(-(double)(x - N / 2) * (x - N / 2) * c);
+            for (int y = 0; y < N; ++y) gy[(size_t)i * N + y] = (float)g[y];  // the same profile along y
+            for (int k = 0; k < N; ++k) {
+                // sum_x g(x) exp(-2 pi i k x / N) with g symmetric about N/2: (-1)^k sum_d g(N/2 + d) cos(2 pi k d / N)
+                double re = 0.0;
+                for (int x = 0; x < N; ++x) re += g[x] * cs[(size_t)((long long)k * ((x - N / 2 + N) % N) % N)];
+                const double sgn = (k & 1) ? -1.0 : 1.0;
+                fx[(size_t)i * N + k] = make_float2((float)(sgn * re), 0.0f);
+            }
+        }
+        cudaError_t e = cudaDeviceSynchronize();  // no launch in flight still reads the previous table
+        if (e == cudaSuccess) e = cudaMemcpy(p->src_fx, fx.data(), sizeof(float2) * fx.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->src_gy, gy.data(), sizeof(float) * gy.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_check(e, "ts_plan_set_sources");
+    }
     return TS_OK;
 }
 

@@ -71,6 +71,8 @@ struct Plan {
     double2* shy_mean = nullptr;  // [3] mean_j (cos, sin)(dkappa_p y_j), FP64
     double* shb = nullptr;     // [S][27] subharmonic amplitudes sqrt(Phi_phi) dkappa_p, FP64
     float2* tilt = nullptr;    // [2][N] AR translation factors (x then y), rebuilt per call
+    float2* src_fx = nullptr;  // [kMaxSources][N] row DFT of each source's x profile (N = 512, 1024), FP64-built
+    float* src_gy = nullptr;   // [kMaxSources][N] each source's y profile (N = 512, 1024), FP64-built
 
     // workspace
     float2* ws_y = nullptr;       // [screen_chunk][N][N] column-transformed screen spectra
@@ -136,7 +138,10 @@ cudaError_t tc_row_pass(int flags, const RowParams& rp, int B, long long budget,
 cudaError_t tc_col_pass(int groups, bool conj, bool sep, const ColParams& cp, int B, long long budget, int* err,
                         cudaStream_t st);
 cudaError_t prepare_tc_prop();
-cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st);
+// source = true: the first column pass generates its input from the plan's sources (fields
+// src_off + b), see ColParams; cudaErrorNotSupported where the kernels cannot, before any launch
+cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st,
+                            bool source = false, int src_off = 0);
 cudaError_t prepare_prop_kernels(int N);
 cudaError_t prepare_screen_kernels(int N);
 cudaError_t launch_row_sums(const Plan& p, const double* rows, int B, double* out, cudaStream_t st);

@@ -62,7 +62,8 @@ cudaError_t launch_row_pass(const Plan& p, int flags, const RowArgs& a, cudaStre
     }
 }
 
-cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st)
+cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, int B, cudaStream_t st, bool source,
+                            int src_off)
 {
     ColParams cp{};
     cp.field = field;
@@ -77,13 +78,18 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
     cp.budget = p.tc_budget;
     cp.tiny_cross = p.tiny_cross;
     cp.stall = p.test_stall ? 1 : 0;
+    cp.src_fx = p.src_fx;
+    cp.src_gy = p.src_gy;
+    cp.n_src = p.n_src;
+    cp.src_off = src_off;
+    if (source && (p.split_bf16 || p.src_fx == nullptr || p.n_src < 1)) return cudaErrorNotSupported;
     if (p.split_bf16) return tc_col_pass(p.tc_col_groups, conj, p.sep_transfer, cp, B, p.tc_budget, p.d_err, st);
     switch (p.N) {
-    case 128: return col_pass_n<128>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
-    case 256: return col_pass_n<256>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
-    case 512: return col_pass_n<512>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
-    case 1024: return col_pass_n<1024>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
-    case 2048: return col_pass_n<2048>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st);
+    case 128: return col_pass_n<128>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st, source);
+    case 256: return col_pass_n<256>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st, source);
+    case 512: return col_pass_n<512>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st, source);
+    case 1024: return col_pass_n<1024>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st, source);
+    case 2048: return col_pass_n<2048>(p.fft_e, p.col_variant, conj, p.sep_transfer, cp, B, st, source);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -37,6 +37,12 @@ struct ColParams {
     long long budget;  // clock64 cycles such a wait may take
     bool tiny_cross;   // separable form with the cross term e <= 0.01 rad: exp(-i e) to second order
     int stall;         // test hook: the prefetching pass skips its first copy (its first wait runs out)
+    // source mode of the prefetching column pass (the first step of a call with TS_PROP_SOURCE): the
+    // input R0 = FFT_rows(U0) of field b is generated in registers as the rank-one product
+    // src_fx[s][kx] * src_gy[s][y], s = (b + src_off) mod n_src
+    const float2* src_fx;  // [kMaxSources][N] row DFTs of the sources' x profiles (FP64-built)
+    const float* src_gy;   // [kMaxSources][N] the sources' y profiles exp(-(y - N/2)^2 dx^2 / w0^2), or 1
+    int n_src, src_off;
 };
 
 // Per-N entry points, instantiated in ts_prop_n<N>.cu (one translation unit per N builds in parallel).
@@ -51,7 +57,10 @@ cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B
 // and 3 (N = 1024, E = 32): persistent CTAs whose next 64 KiB / 32 KiB tile arrives by TMA while the
 // current one is transformed
 template <int N>
-cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st);
+// source = true: the first column pass of a call that starts from the sources, generating its input
+// (prefetching variants only; cudaErrorNotSupported otherwise, and the caller runs the first row pass)
+cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st,
+                       bool source);
 template <int N>
 cudaError_t prepare_prop_n();
 
@@ -88,7 +97,8 @@ cudaError_t build_ht_table(float4* ht, const float2* P, int S, double dk, cudaSt
 // the TMA-prefetching passes (ts_prop_tma.cu), N = 512 and 1024 at 32 points per thread;
 // cudaErrorNotSupported when the arguments do not fit them.  w = columns per CTA (N = 1024: 8, two
 // CTAs per SM, or 4, four per SM; N = 512: 16)
-cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st);
+cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st,
+                         bool source = false);
 cudaError_t row_pass_tma(int N, int flags, const RowParams& rp, int B, cudaStream_t st);
 cudaError_t prepare_prop_tma(int N);
 

@@ -349,15 +349,20 @@ EncodeTiledFn encode_fn()
 template <int HMODE>
 cudaError_t fused_launch(const FusedParams& fp, const CUtensorMap& map, cudaStream_t st)
 {
-    static int resident = 0;
+    // CTAs resident on the current device at once, cached per device ordinal (below 64)
+    static int cache[64] = {};
+    int dev = 0, resident = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) resident = cache[dev];
     if (resident == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int sms = 0, per = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prop_fused_kernel<HMODE>, Fused::THREADS, Fused::smem);
         if (e != cudaSuccess) return e;
         resident = sms * per;
+        if (dev >= 0 && dev < 64) cache[dev] = resident;
     }
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     const int items = (2 * fp.S + 1) * fp.B * Fused::TPF;

@@ -543,15 +543,17 @@ cudaError_t row_pass_n(int E, int variant, int flags, const RowParams& rp, int B
 }
 
 template <int N>
-cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams& cp, int B, cudaStream_t st,
+                       bool source)
 {
     if constexpr (N == 512 || N == 1024) {
         if ((variant == 2 || variant == 3) && E == 32) {
             const int w = N == 512 ? 16 : (variant == 2 ? 8 : 4);
-            cudaError_t e = col_pass_tma(N, w, conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st);
-            if (e != cudaErrorNotSupported) return e;
+            cudaError_t e = col_pass_tma(N, w, conj, sep ? (cp.tiny_cross ? 2 : 1) : 0, cp, B, st, source);
+            if (e != cudaErrorNotSupported || source) return e;
         }
     }
+    if (source) return cudaErrorNotSupported;
     if constexpr (N == 1024) {
         if (variant == 1 && E == 32) {
             if (sep) return conj ? col_launch_warp<N, true, true>(cp, B, st) : col_launch_warp<N, false, true>(cp, B, st);

@@ -3,6 +3,6 @@
 
 namespace ts {
 template cudaError_t row_pass_n<1024>(int, int, int, const RowParams&, int, cudaStream_t);
-template cudaError_t col_pass_n<1024>(int, int, bool, bool, const ColParams&, int, cudaStream_t);
+template cudaError_t col_pass_n<1024>(int, int, bool, bool, const ColParams&, int, cudaStream_t, bool);
 template cudaError_t prepare_prop_n<1024>();
 }  // namespace ts

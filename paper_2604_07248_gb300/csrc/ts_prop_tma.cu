@@ -58,7 +58,7 @@ struct ColTma {
     static_assert(PER_SM * (smem + 1024) <= 228 * 1024, "resident CTAs fit the SM's shared memory");
 };
 
-template <bool CONJ, int HMODE, class CT>
+template <bool CONJ, int HMODE, class CT, bool SRC = false>
 __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
     col_pass_tma_kernel(const ColParams a, const __grid_constant__ CUtensorMap tmap, int B)
 {
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
-        if (!a.stall) issue(tile);
+        if (!SRC && !a.stall) issue(tile);
     }
     stage_twiddles_c<C>(tw, a.tw);
     for (int i = tid; i < N; i += CT::THREADS) {
@@ -102,18 +102,30 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
     uint32_t parity = 0;
     for (; tile < tiles; tile += gridDim.x, parity ^= 1u) {
         const int b = tile / TPF, col = (tile % TPF) * W + c;
-        const bool ok = mbar_wait(bar, parity, a.budget);
         float2 v[32];
-        if (ok) {
+        if constexpr (SRC) {
+            // the source's row transform: a rank-one product, no input to load
+            const int s = (b + a.src_off) % a.n_src;
+            const float2 fx = __ldg(a.src_fx + (size_t)s * N + col);
+            const float* gy = a.src_gy + (size_t)s * N;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = buf[(t + T * i) * W + c];
-        }
-        if (__syncthreads_or(!ok)) {  // every thread has read the tile before the exchange reuses it
-            if (tid == 0) {
-                atomicExch(a.err, kErrTmaWait);
-                mbar_wait(bar, parity, a.budget);  // the copy in flight, bounded again
+            for (int i = 0; i < 32; ++i) {
+                const float g = __ldg(gy + t + T * i);
+                v[i] = make_float2(fx.x * g, fx.y * g);
             }
-            return;
+        } else {
+            const bool ok = mbar_wait(bar, parity, a.budget);
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = buf[(t + T * i) * W + c];
+            }
+            if (__syncthreads_or(!ok)) {  // every thread has read the tile before the exchange reuses it
+                if (tid == 0) {
+                    atomicExch(a.err, kErrTmaWait);
+                    mbar_wait(bar, parity, a.budget);  // the copy in flight, bounded again
+                }
+                return;
+            }
         }
         float2* line = buf + c * CT::LS;
         fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
             transfer_tile_tab<CONJ, HMODE, decltype(tab), T>(v, tab, col, t, a.ccross, a.dcoef, a.inv_k2);
         }
         fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
-        if (tid == 0 && tile + (int)gridDim.x < tiles) {
+        if (!SRC && tid == 0 && tile + (int)gridDim.x < tiles) {
             fence_proxy_async();
             issue(tile + gridDim.x);
         }
@@ -269,19 +281,23 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// CTAs resident per SM for a kernel (cached per kernel address and device)
+// CTAs of a kernel resident on the current device at once (SMs x CTAs per SM), cached per device in
+// `cache` (one slot per device ordinal below kMaxDevices; larger ordinals are queried every time)
+constexpr int kMaxDevices = 64;
 template <class K>
-int max_ctas(K kernel, int threads, size_t smem)
+int max_ctas(K kernel, int threads, size_t smem, int (&cache)[kMaxDevices])
 {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < kMaxDevices && cache[dev] > 0) return cache[dev];
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev] = sms * per;
     return sms * per;
 }
 
 
-template <bool CONJ, int HMODE, class CT>
+template <bool CONJ, int HMODE, class CT, bool SRC = false>
 cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
 {
     constexpr int N = CT::N, W = CT::W;
@@ -295,19 +311,28 @@ cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, cp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    static int resident = 0;
-    if (resident == 0) resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, CT>, CT::THREADS, CT::smem);
+    static int cache[kMaxDevices] = {};
+    const int resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, CT, SRC>, CT::THREADS, CT::smem, cache);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     // full residency, tiles strided over the CTAs: the CTAs an SM holds share its issue slots, so
     // filling every slot keeps each SM's tile count within one of the mean
     const int grid = std::min(B * CT::TPF, resident);
-    col_pass_tma_kernel<CONJ, HMODE, CT><<<grid, CT::THREADS, CT::smem, st>>>(cp, map, B);
+    col_pass_tma_kernel<CONJ, HMODE, CT, SRC><<<grid, CT::THREADS, CT::smem, st>>>(cp, map, B);
     return cudaGetLastError();
 }
 
 template <class CT>
-cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st, bool source)
 {
+    if (source) {  // forward only: the first column pass of a call that starts from the sources
+        if (conj || cp.src_fx == nullptr || cp.src_gy == nullptr || cp.n_src < 1) return cudaErrorNotSupported;
+        switch (hmode) {
+        case 0: return col_launch_tma<false, 0, CT, true>(cp, B, st);
+        case 1: return col_launch_tma<false, 1, CT, true>(cp, B, st);
+        case 2: return col_launch_tma<false, 2, CT, true>(cp, B, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (hmode * 2 + (conj ? 1 : 0)) {
     case 0: return col_launch_tma<false, 0, CT>(cp, B, st);
     case 1: return col_launch_tma<true, 0, CT>(cp, B, st);
@@ -322,8 +347,8 @@ cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, c
 template <class RT, int FLAGS>
 cudaError_t row_launch_tma(const RowParams& rp, int B, cudaStream_t st)
 {
-    static int resident = 0;
-    if (resident == 0) resident = max_ctas(row_pass_tma_kernel<RT, FLAGS>, RT::THREADS, RT::smem);
+    static int cache[kMaxDevices] = {};
+    const int resident = max_ctas(row_pass_tma_kernel<RT, FLAGS>, RT::THREADS, RT::smem, cache);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
     const int units = B * RT::N / RT::RPW;
     const int grid = std::min((units + RT::WARPS - 1) / RT::WARPS, resident);  // full residency
@@ -352,12 +377,13 @@ cudaError_t tma_attr(K kernel, size_t bytes)
 
 }  // namespace
 
-cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st)
+cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp, int B, cudaStream_t st,
+                         bool source)
 {
     if ((reinterpret_cast<uintptr_t>(cp.field) & 15) != 0 || cp.err == nullptr) return cudaErrorNotSupported;
-    if (N == 1024 && w == 8) return col_dispatch_tma<ColTma<1024, 8>>(conj, hmode, cp, B, st);
-    if (N == 1024 && w == 4) return col_dispatch_tma<ColTma<1024, 4>>(conj, hmode, cp, B, st);
-    if (N == 512 && w == 16) return col_dispatch_tma<ColTma<512, 16>>(conj, hmode, cp, B, st);
+    if (N == 1024 && w == 8) return col_dispatch_tma<ColTma<1024, 8>>(conj, hmode, cp, B, st, source);
+    if (N == 1024 && w == 4) return col_dispatch_tma<ColTma<1024, 4>>(conj, hmode, cp, B, st, source);
+    if (N == 512 && w == 16) return col_dispatch_tma<ColTma<512, 16>>(conj, hmode, cp, B, st, source);
     return cudaErrorNotSupported;
 }
 
@@ -384,6 +410,9 @@ void col_attrs(cudaError_t& e)
     chk(tma_attr(col_pass_tma_kernel<true, 1, CT>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<false, 2, CT>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<true, 2, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 0, CT, true>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 1, CT, true>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 2, CT, true>, CT::smem));
 }
 template <class RT>
 void row_attrs(cudaError_t& e)

@@ -35,8 +35,12 @@ def make_instances(specs, seed):
 
 
 def test_batch_equals_per_instance_propagation(monkeypatch):
-    # per-instance passes with the same points per thread as the batch kernel: identical arithmetic
+    # per-instance passes with the same points per thread and the same (per-CTA) pass kernels as the
+    # batch kernel's tiles: identical arithmetic
     monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "0")
+    monkeypatch.setenv("TS_ROW_VARIANT", "0")
+    monkeypatch.setenv("TS_FUSED", "0")
     specs = [(256, 4, 1e-15), (512, 7, 3e-15), (1024, 5, 1e-14), (2048, 4, 1e-16), (512, 12, 1e-14),
              (256, 20, 2e-16), (1024, 9, 5e-15)]
     seed = W.SEED_BASE + 4

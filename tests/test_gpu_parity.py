@@ -482,6 +482,39 @@ def test_prefetching_passes_at_512_match_oracle(B, phi_group, monkeypatch):
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
+@pytest.mark.parametrize("N,dx,groups", [(1024, 5e-4, 1), (1024, 5e-4, 2), (512, 1e-3, 2)])
+def test_sources_generated_in_the_first_column_pass(N, dx, groups, monkeypatch):
+    # with TS_PROP_SOURCE and the prefetching column pass, the first row pass is skipped: the column
+    # pass builds the row transform of each source (Gaussians and a plane wave, cycling over 3
+    # sources; with two concurrent field groups the second starts at source 2) from an FP64 table
+    monkeypatch.setenv("TS_FFT_E", "32")
+    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_ROW_VARIANT", "2")
+    monkeypatch.setenv("TS_PROP_STREAMS", str(groups))
+    monkeypatch.setenv("TS_FUSED", "0")
+    S, B, dz = 2, 4, 60.0
+    w0 = [0.01, 0.0, 0.017]
+    md = omedium(N, dx)
+    plan = ts.Plan(LAM, N, dx, [dz] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
+    plan.set_sources(w0)
+    phis = np.stack([O.make_screen(md, 1e-14, dz, 0, 81, s, 0) for s in range(S)])
+    ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
+    U = cfield(B, N)
+    plan.timing(True, capacity=8)
+    plan.propagate(U, B, phasor=ph, phi_group=B, flags=ts.TS_PROP_SOURCE)
+    plan.device_status()
+    n_row, _ = plan.timing_read(1)
+    plan.timing(False)
+    assert n_row == groups * S  # no first row pass: S row passes per group
+    set_phi = np.angle(np.exp(1j * phis))
+    got = U.cpu().numpy()
+    for b in range(B):
+        w = w0[b % 3]
+        src = O.source_gaussian(N, dx, w) if w > 0 else np.ones((N, N), np.complex128)
+        ref = O.propagate(md, [dz] * S, set_phi, src)
+        assert rel_l2(got[b], ref) < TOL, (b, rel_l2(got[b], ref))
+
+
 def test_prefetching_column_pass_with_the_series_cross_term(monkeypatch):
     # dz = 2500 m at dx = 0.5 mm (above the Eq. 7 limit, so the plan allows aliasing): the cross term
     # reaches 0.015 rad, the separable transfer function applies exp(-i e) as its short series
