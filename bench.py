@@ -437,8 +437,9 @@ def run_gpu(args):
     loop_gbs = loop_bytes / (ms_loop * 1e-3) / 1e9
     roof["split_step_loop"] = {"algorithmic_bytes": int(loop_bytes), "us_per_call": round(ms_loop * 1e3, 2),
                                "achieved": round(loop_gbs, 1), "frac": round(loop_gbs / peak, 4), "calls": n_loop,
-                               "note": "ts_propagate of the 8 beams through 16 resident phasor screens (first row "
-                                       "pass + 16 column and row passes), as configured by the autotuner"}
+                               "note": "ts_propagate of the 8 beams through 16 resident phasor screens (16 column "
+                                       "and row passes; the sources are generated in the first column pass), as "
+                                       "configured by the autotuner"}
 
     # the whole timed step against the same peak: algorithmic bytes of one step (AR update + synthesis
     # of the S screens, propagation of the B beams) / device time per step
