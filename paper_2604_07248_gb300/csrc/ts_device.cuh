@@ -72,6 +72,21 @@ __device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb)
     return make_float2(-rad * c, -rad * s);
 }
 
+// exp(i phi) for a screen phase: phi reduced to [-pi, pi] by the nearest multiple of 2 pi with a
+// two-part 2 pi (hi = fl(2 pi), lo = 2 pi - hi, so the reduction error stays below 1e-7 rad for
+// |phi| < 1e4), then the hardware sine / cosine, accurate to about 4e-7 on that interval.  The screen
+// synthesis (phasor screens) and the row pass (float screens) both use it, so the two give the same
+// fields bit for bit.
+__device__ __forceinline__ float2 expi_phase(float phi)
+{
+    const float kq = rintf(phi * 0.159154943091895336f);
+    float r = fmaf(-kq, 6.28318548202514648f, phi);
+    r = fmaf(-kq, -1.74845553e-7f, r);
+    float s, c;
+    __sincosf(r, &s, &c);
+    return make_float2(c, s);
+}
+
 __device__ __forceinline__ double u01d(uint32_t w) { return ((double)(w >> 8) + 0.5) * 5.9604644775390625e-8; }
 
 __device__ __forceinline__ double2 box_muller_d(uint32_t wa, uint32_t wb)

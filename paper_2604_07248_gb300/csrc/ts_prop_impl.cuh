@@ -76,9 +76,8 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
             const float* ph = a.phi + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * N;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
-                float s, c;
-                sincosf(__ldg(ph + t + i * T), &s, &c);
-                v[i] = cmul(v[i], make_float2(c, a.phase_sign * s));
+                const float2 e = expi_phase(__ldg(ph + t + i * T));
+                v[i] = cmul(v[i], make_float2(e.x, a.phase_sign * e.y));
             }
         }
     }

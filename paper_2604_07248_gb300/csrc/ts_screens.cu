@@ -168,11 +168,7 @@ __global__ void __launch_bounds__(SRowCfg<N>::THREADS) screen_row_kernel(const S
     }
     if (a.phasor != nullptr) {
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            float sn, cs;
-            sincosf(v[i].x, &sn, &cs);
-            a.phasor[roff + t + i * T] = make_float2(cs, sn);
-        }
+        for (int i = 0; i < E; ++i) a.phasor[roff + t + i * T] = expi_phase(v[i].x);
     }
 }
 

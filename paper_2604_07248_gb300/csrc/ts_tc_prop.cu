@@ -276,9 +276,8 @@ __global__ void __launch_bounds__(128, kRowPerSm) tc_row_kernel(const RowParams 
                 const float* ph = a.phi + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * kTN;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    float s, c;
-                    sincosf(__ldg(ph + lane + 32 * i), &s, &c);
-                    v[i] = cmul(v[i], make_float2(c, a.phase_sign * s));
+                    const float2 e = expi_phase(__ldg(ph + lane + 32 * i));
+                    v[i] = cmul(v[i], make_float2(e.x, a.phase_sign * e.y));
                 }
             }
         }
