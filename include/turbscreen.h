@@ -176,7 +176,11 @@ double ts_max_step(const ts_medium* medium, const ts_grid* grid);
 
 /* Source table used by ts_propagate with TS_PROP_SOURCE: field b starts as source (b mod n).
  * w0[k] > 0: collimated Gaussian exp(-r^2 / w0^2) centred on pixel (N/2, N/2) (S22);
- * w0[k] <= 0: unit plane wave (Sec. 3.3).  w0 is a HOST array of n entries (n <= 64). */
+ * w0[k] <= 0: unit plane wave (Sec. 3.3).  w0 is a HOST array of n entries (n <= 64).  For N = 512
+ * and 1024 it also builds, in FP64 on the host, each source's row transform (the sources are
+ * separable), from which the first column pass of a call starts; it then waits for the device and
+ * copies the tables synchronously, so call it outside stream capture and not while a ts_propagate of
+ * the plan is in flight on another thread. */
 ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0);
 
 /* Source fields (S22; plane wave of Sec. 3.3): writes the plan's source table into field
