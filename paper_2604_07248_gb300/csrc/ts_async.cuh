@@ -129,5 +129,40 @@ __device__ __forceinline__ void transfer_tile(float2 (&v)[32], const float4* ht,
     transfer_tile_tab<CONJ, HMODE>(v, [ht](int m) { return ht[m]; }, col, t, ccross, dcoef, inv_k2);
 }
 
+// ---- host: the TMA tensor map of a batch of N x N complex64 fields, viewed as (2N floats) x (B N
+// rows), with boxes of box_rows rows x box_floats floats (the driver's encoder, reached through the
+// runtime's entry-point query, so no link against the driver library is needed) ----
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    return fn;
+}
+
+// cudaErrorNotSupported when the encoder is unavailable, cudaErrorInvalidValue when it rejects the map
+inline cudaError_t field_tensor_map(CUtensorMap* map, void* field, int N, int B, int box_floats, int box_rows)
+{
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * N, (cuuint64_t)B * N};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * N * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_floats, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 }  // namespace async
 }  // namespace ts

@@ -329,22 +329,6 @@ __global__ void ht_table_kernel(float4* ht, const float2* P, int S, float dk)
     }
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
-        return reinterpret_cast<EncodeTiledFn>(ptr);
-    }();
-    return fn;
-}
 
 template <int HMODE>
 cudaError_t fused_launch(const FusedParams& fp, const CUtensorMap& map, cudaStream_t st)
@@ -385,16 +369,9 @@ cudaError_t prop_fused_1024(int hmode, const FusedParams& fp, cudaStream_t st)
         (fp.set_stride & 1) != 0 || fp.err == nullptr || fp.done == nullptr || fp.B < 1 ||
         fp.S < 1 || fp.S > kMaxScreens || fp.n_src < 1)
         return cudaErrorNotSupported;
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)2 * kN, (cuuint64_t)fp.B * kN};
-    const cuuint64_t strides[1] = {(cuuint64_t)2 * kN * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * Fused::W), 256u};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, fp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    cudaError_t em = field_tensor_map(&map, fp.field, kN, fp.B, 2 * Fused::W, 256);
+    if (em != cudaSuccess) return em;
     FusedParams f = fp;
     f.head = fp.done + (2 * fp.S + 1) * fp.B;  // the work counter follows the completion counters
     cudaError_t e = cudaMemsetAsync(f.done, 0, sizeof(int) * ((2 * f.S + 1) * f.B + 1), st);

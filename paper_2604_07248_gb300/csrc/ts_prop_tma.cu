@@ -264,22 +264,6 @@ __global__ void __launch_bounds__(RT::THREADS, 2) row_pass_tma_kernel(const RowP
 // ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
-        return reinterpret_cast<EncodeTiledFn>(ptr);
-    }();
-    return fn;
-}
 
 // CTAs of a kernel resident on the current device at once (SMs x CTAs per SM), cached per device in
 // `cache` (one slot per device ordinal below kMaxDevices; larger ordinals are queried every time)
@@ -300,17 +284,9 @@ int max_ctas(K kernel, int threads, size_t smem, int (&cache)[kMaxDevices])
 template <bool CONJ, int HMODE, class CT, bool SRC = false>
 cudaError_t col_launch_tma(const ColParams& cp, int B, cudaStream_t st)
 {
-    constexpr int N = CT::N, W = CT::W;
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)2 * N, (cuuint64_t)B * N};
-    const cuuint64_t strides[1] = {(cuuint64_t)2 * N * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * W), (cuuint32_t)CT::BOX_ROWS};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, cp.field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    cudaError_t e = field_tensor_map(&map, cp.field, CT::N, B, 2 * CT::W, CT::BOX_ROWS);
+    if (e != cudaSuccess) return e;
     static int cache[kMaxDevices] = {};
     const int resident = max_ctas(col_pass_tma_kernel<CONJ, HMODE, CT, SRC>, CT::THREADS, CT::smem, cache);
     if (resident <= 0) return cudaErrorInvalidConfiguration;
