@@ -32,6 +32,23 @@ namespace {
 using namespace async;
 constexpr int kErrTmaWait = 4;  // error word value: a prefetch wait ran out of its budget
 
+// Stage 0 of a 1024-point line FFT (32 x 32, thread t holds points t + 32 i) with its exchange in
+// 16-byte stores: thread t's 32 stage outputs land at line[34 t + r] (two float2 of padding per 32
+// points, so pairs r, r + 1 are 16-byte aligned) and come back as line[t + 34 i].  With the line
+// strides the passes choose, stores and loads run at their wavefront minimum (4 and 2 per warp).
+template <int SIGN, class Bar>
+__device__ __forceinline__ void stage0_exchange_x4(float2 (&v)[32], float2* line, int t, Bar bar)
+{
+    Dft<32, SIGN>::run(v);
+    float4* w = reinterpret_cast<float4*>(line + 34 * t);
+#pragma unroll
+    for (int r = 0; r < 32; r += 2) w[r / 2] = make_float4(v[r].x, v[r].y, v[r + 1].x, v[r + 1].y);
+    bar();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = line[t + 34 * i];
+    bar();
+}
+
 // ---------------------------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------------------------
@@ -45,7 +62,10 @@ struct ColTma {
     static constexpr int T = C::T, THREADS = T * W, PER_SM = 512 / THREADS, BOX_ROWS = 256;
     static constexpr bool SPLIT = PER_SM > 2;
     static constexpr int TPF = N / W;                        // tiles per field
-    static constexpr int LS = C::padded + (16 / W > 1 ? 16 / W : 1);  // column stride of the exchange buffer
+    // column stride of the exchange buffer (float2).  N = 1024 uses the 16-byte exchange: LS >= 1086,
+    // and LS / 2 odd (8 columns) or = 2 mod 8 (4 columns) keeps both its 16-byte stores and its 8-byte
+    // loads at the minimum number of shared-memory wavefronts
+    static constexpr int LS = N == 1024 ? (W == 4 ? 1092 : 1086) : C::padded + (16 / W > 1 ? 16 / W : 1);
     static constexpr int TILE_BYTES = W * N * 8;
     static constexpr size_t off_ht = sizeof(float2) * C::tw_smem;
     static constexpr size_t ht_bytes = SPLIT ? (sizeof(float2) + sizeof(float)) * N : sizeof(float4) * N;
@@ -128,7 +148,10 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
             }
         }
         float2* line = buf + c * CT::LS;
-        fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
+        if constexpr (N == 1024)
+            stage0_exchange_x4<-1>(v, line, t, BlockBar());
+        else
+            fft_stage_c<C, 0, -1>(v, line, t, tw, BlockBar());
         fft_stage_c<C, 1, -1>(v, line, t, tw, BlockBar());
         if constexpr (CT::SPLIT) {
             auto tab = [hp, hk](int m) {
@@ -140,7 +163,11 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
             auto tab = [ht](int m) { return ht[m]; };
             transfer_tile_tab<CONJ, HMODE, decltype(tab), T>(v, tab, col, t, a.ccross, a.dcoef, a.inv_k2);
         }
-        fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());  // ends with a barrier after the last read
+        // stage 0 of the inverse: ends with a barrier after the last read
+        if constexpr (N == 1024)
+            stage0_exchange_x4<+1>(v, line, t, BlockBar());
+        else
+            fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());
         if (!SRC && tid == 0 && tile + (int)gridDim.x < tiles) {
             fence_proxy_async();
             issue(tile + gridDim.x);
@@ -161,7 +188,8 @@ struct RowTma {
     using C = FftCfg<N, 32>;  // T = N / 32 threads per row, 32 / T rows per warp
     static constexpr int T = C::T, RPW = 32 / T;
     static constexpr int WARPS = 8, THREADS = 32 * WARPS;
-    static constexpr int LS = C::padded;  // line stride (float2); a line holds the dense row or the exchange
+    // line stride (float2); a line holds the dense row or the exchange (N = 1024: the 16-byte exchange)
+    static constexpr int LS = N == 1024 ? 1086 : C::padded;
     static constexpr int ROW_BYTES = N * 8;
     static constexpr size_t off_line = sizeof(float2) * C::tw_smem;
     static constexpr size_t off_bar = off_line + sizeof(float2) * WARPS * RPW * LS;
@@ -216,7 +244,10 @@ __global__ void __launch_bounds__(RT::THREADS, 2) row_pass_tma_kernel(const RowP
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = line[t + T * i];
         __syncwarp();  // every lane has its points before the exchange overwrites the rows
-        fft_stage_c<C, 0, +1>(v, line, t, tw, WarpBar());
+        if constexpr (N == 1024)
+            stage0_exchange_x4<+1>(v, line, t, WarpBar());
+        else
+            fft_stage_c<C, 0, +1>(v, line, t, tw, WarpBar());
         if (lane == 0) {  // the lines are free: the step's screen phasor rows come in under the next stage
             const int set = (b + a.phi_off) / a.phi_group;
             const float2* src = a.phasor + (long long)set * a.phi_set_stride + (size_t)j0 * N;
@@ -243,7 +274,10 @@ __global__ void __launch_bounds__(RT::THREADS, 2) row_pass_tma_kernel(const RowP
         }
         __syncwarp();
         if constexpr (FLAGS & RP_OUT_FREQ) {
-            fft_stage_c<C, 0, -1>(v, line, t, tw, WarpBar());
+            if constexpr (N == 1024)
+                stage0_exchange_x4<-1>(v, line, t, WarpBar());
+            else
+                fft_stage_c<C, 0, -1>(v, line, t, tw, WarpBar());
             if (lane == 0 && u + stride < units) {
                 fence_proxy_async();
                 load_rows(u + stride);
