@@ -410,11 +410,24 @@ def run_gpu(args):
         barrier()
         tc_plan.device_status()
         ms_tc = max_over_ranks(g0.elapsed_time(g1))
+        # per-launch device time of the tensor-core passes (CUDA events the library records on the
+        # launching stream), averaged over the passes of 32 more steps
+        n_tm = min(n_tc, 32)
+        tc_plan.timing(True, capacity=n_tm * (S + 1))
+        for _ in range(n_tm):
+            step(tc_plan)
+        barrier()
+        tc_kernels = {}
+        for k, name in ((0, "tc_col_pass"), (1, "tc_row_pass")):
+            n, tot = tc_plan.timing_read(k)
+            if n:
+                tc_kernels[name] = {"launches": n, "avg_us": round(tot / n * 1e3, 3)}
+        tc_plan.timing(False)
         split = {"value": round(n_tc * B * S * world / (ms_tc * 1e-3), 1), "unit": UNIT, "steps": n_tc,
                  "ms_per_step": round(ms_tc / n_tc, 5), "dtype": "bf16 hi+lo split, f32 accumulate",
                  "rel_l2_vs_fp32_per_frame_max": float(f"{max(rel):.3e}"),
                  "rel_l2_vs_fp32_per_frame": [float(f"{r:.3e}") for r in rel], "rel_l2_tolerance": 2e-3,
-                 "streams": tc_plan.tuning()[3],
+                 "streams": tc_plan.tuning()[3], "kernels": tc_kernels,
                  "note": "same workload and screens, AR update + 16 screens + 8 beams per step; column and "
                          "row passes on tcgen05 (32 x 32 four-step DFT)"}
         tc_plan.close()
