@@ -140,6 +140,15 @@ def algorithmic_bytes(N, B, S, source_in_column=False):
     return {0: col, 1: row_avg, 2: screens, 3: fused}
 
 
+def tuning_summary(plan):
+    """The autotuner's choice for a plan and its candidate table (us per column + row pass)."""
+    t = plan.tuning()
+    return {"points_per_thread": t[0], "col_variant": t[5], "row_variant": t[7], "streams": t[3],
+            "us_streams_1_2_4": [round(x, 2) for x in t[4]],
+            "fused": bool(plan.tuning_fused()[0]),
+            "candidates_e_col_row_us": [[e, cv, rv, round(us, 2)] for e, cv, rv, us in plan.tuning_candidates() if us > 0]}
+
+
 def hbm_peak():
     """(GB/s, source) of the HBM roofline denominator: the measured copy bandwidth, else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -710,6 +719,7 @@ def run_monte_carlo(args):
            "config": {"workload": "monte-carlo N=512 S=10 SH3, 8 Cn2, plane + Gaussian 2 cm", "N": N, "dx": wl.dx,
                       "L": wl.L, "screens": S, "realizations_per_step": Rc, "fields_per_step": B,
                       "screens_per_step": Rc * S, "field_screen_steps_per_step": B * S,
+                      "autotune": tuning_summary(plans[0]),
                       "note": "SI of the plane wave over the whole grid; subharmonic screens are not periodic, "
                               "so the periodic grid adds seam scintillation above sigma_R^2 (informational)"},
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
@@ -789,7 +799,7 @@ def run_d2nn(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (loss f64)", "data": "synthetic",
            "config": {"workload": "d2nn N=512 S=10 B=64, MAE loss, screens regenerated from the seed", "N": N,
                       "dx": wl.dx, "L": wl.L, "screens": S, "batch": B, "aperture_m": AP,
-                      "field_screen_steps_per_step": 2 * B * S},
+                      "field_screen_steps_per_step": 2 * B * S, "autotune": tuning_summary(plan)},
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
                         "scope": "whole step (all kernels), algorithmic bytes per step / device time per step",

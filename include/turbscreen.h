@@ -138,8 +138,10 @@ size_t ts_plan_device_bytes(ts_plan plan);
  *  - `streams` = number of field groups ts_propagate runs concurrently on the plan's own streams when
  *    the screens are given (1, 2 or 4; forked from and joined back to the caller's stream);
  *    us_streams[3] receives the timed cost for 1, 2 and 4 groups.
- * Outputs other than points_per_thread may be NULL; a 0 timing means not timed (N <= 256, a cached
- * result, or TS_FFT_E / TS_COL_VARIANT / TS_ROW_VARIANT / TS_PROP_STREAMS set in the environment). */
+ * Each timing is the fastest of three interleaved rounds over the candidates (2 warm-up + 5 timed
+ * repetitions each).  Outputs other than points_per_thread may be NULL; a 0 timing means not timed
+ * (N <= 256, a cached result, or TS_FFT_E / TS_COL_VARIANT / TS_ROW_VARIANT / TS_PROP_STREAMS set in
+ * the environment). */
 ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, float* us_e32, int* streams,
                          float* us_streams, int* col_variant, float* us_e32_warp_columns, int* row_variant,
                          float* us_e32_shared_phasor_rows);

@@ -272,9 +272,15 @@ ts_status propagate_groups(Plan& p, float2* U, int B, const float* phi, const vo
 
 // Autotuner: for N >= 512 the propagation passes exist with E = 16 and E = 32 points per thread
 // (different register / occupancy / exchange trade-offs).  Each candidate runs one column pass and
-// one middle row pass on B_t workspace fields (2 warm-up + 5 timed repetitions, CUDA events) and the
-// faster one is kept.  Results are cached per (device, N, B_t, transfer form); TS_FFT_E=16|32 forces
-// a choice.
+// one middle row pass on B_t workspace fields (2 warm-up + 5 timed repetitions, CUDA events), in
+// kTuneRounds interleaved rounds over the candidates; each candidate's fastest round counts, so a
+// transient (clocks still ramping at the first launches, a co-tenant's burst) cannot decide the
+// choice.  Results are cached per (device, N, B_t, transfer form); TS_FFT_E=16|32 forces a choice.
+constexpr int kTuneRounds = 3;
+// fields per timed pass in the first two stages: the plan's batch up to 32 (a plan for many fields,
+// e.g. 64 Monte Carlo beams at N = 512, is timed at a batch that behaves like its own; the
+// workspace holds screen_chunk >= this many fields)
+constexpr int kTuneBatch = 32;
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 
@@ -324,7 +330,7 @@ ts_status autotune(Plan& p)
         return TS_OK;
     }
     const size_t N2 = (size_t)p.N * p.N;
-    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
+    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), kTuneBatch));
     const auto key =
         std::make_tuple(p.device, p.N, Bt, (p.sep_transfer ? 1 : 0) + 2 * (force_e + 64 * (force_v + 1) + 256 * (force_r + 1)));
     {
@@ -342,41 +348,50 @@ ts_status autotune(Plan& p)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_c = 1;
-    for (int c = 0; c < kCand && e == cudaSuccess; ++c) {
-        if (!use[c]) continue;
-        p.fft_e = cand_e[c];
-        p.col_variant = cand_v[c];
-        p.row_variant = cand_r[c];
-        RowArgs ra{};
-        ra.field = p.ws_y;
-        ra.phasor = p.ws_phi;
-        ra.phi_set_stride = 0;
-        ra.phi_group = Bt;
-        ra.phase_sign = 1.0f;
-        ra.B = Bt;
-        auto once = [&]() {
-            cudaError_t x = launch_col_pass(p, 0, false, p.ws_y, Bt, nullptr);
-            if (x == cudaSuccess) x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, nullptr);
-            return x;
-        };
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = once();
-        if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
-        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = once();
-        if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        p.tune_us[c] = ms * 1000.0f / 5.0f;
-        if (e == cudaSuccess && p.tune_us[c] < best) {
-            best = p.tune_us[c];
-            best_c = c;
+    float t_min[kCand];
+    for (int c = 0; c < kCand; ++c) t_min[c] = 1e30f;
+    for (int rd = 0; rd < kTuneRounds && e == cudaSuccess; ++rd) {
+        for (int c = 0; c < kCand && e == cudaSuccess; ++c) {
+            if (!use[c]) continue;
+            p.fft_e = cand_e[c];
+            p.col_variant = cand_v[c];
+            p.row_variant = cand_r[c];
+            RowArgs ra{};
+            ra.field = p.ws_y;
+            ra.phasor = p.ws_phi;
+            ra.phi_set_stride = 0;
+            ra.phi_group = Bt;
+            ra.phase_sign = 1.0f;
+            ra.B = Bt;
+            auto once = [&]() {
+                cudaError_t x = launch_col_pass(p, 0, false, p.ws_y, Bt, nullptr);
+                if (x == cudaSuccess)
+                    x = launch_row_pass(p, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE, ra, nullptr);
+                return x;
+            };
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+            for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess) t_min[c] = std::min(t_min[c], ms * 1000.0f / 5.0f);
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune");
+    float best = 1e30f;
+    int best_c = 1;
+    for (int c = 0; c < kCand; ++c) {
+        if (!use[c]) continue;
+        p.tune_us[c] = t_min[c];
+        if (t_min[c] < best) {
+            best = t_min[c];
+            best_c = c;
+        }
+    }
     p.fft_e = cand_e[best_c];
     p.col_variant = cand_v[best_c];
     p.row_variant = cand_r[best_c];
@@ -395,7 +410,7 @@ constexpr int kTuneSteps = 4;  // column + row pass pairs per fork in the group 
 ts_status autotune_groups(Plan& p)
 {
     p.prop_groups = 1;
-    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), 8));
+    const int Bt = std::max(1, std::min(std::min(p.max_batch, p.screen_chunk), kTuneBatch));
     if (Bt < 2) return TS_OK;
     if (const char* env = std::getenv("TS_PROP_STREAMS")) {
         const int g = std::atoi(env);
@@ -421,11 +436,11 @@ ts_status autotune_groups(Plan& p)
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int cand[3] = {1, 2, 4};
-    float best = 1e30f;
-    int best_g = 1;
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    float t_min[3] = {1e30f, 1e30f, 1e30f};
+    for (int rd = 0; rd < kTuneRounds * 3 && e == cudaSuccess; ++rd) {  // interleaved rounds, as above
+        const int c = rd % 3;
         const int groups = cand[c];
-        if (groups > Bt) break;
+        if (groups > Bt) continue;
         auto once = [&]() {
             cudaError_t x = cudaEventRecord(p.fork, nullptr);
             for (int g = 1; g < groups && x == cudaSuccess; ++g) x = cudaStreamWaitEvent(p.aux[g - 1], p.fork, 0);
@@ -460,15 +475,20 @@ ts_status autotune_groups(Plan& p)
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        p.tune_group_us[c] = ms * 1000.0f / (5.0f * kTuneSteps);
-        if (e == cudaSuccess && p.tune_group_us[c] < best * 0.97f) {  // prefer fewer streams unless 3 % faster
-            best = p.tune_group_us[c];
-            best_g = groups;
-        }
+        if (e == cudaSuccess) t_min[c] = std::min(t_min[c], ms * 1000.0f / (5.0f * kTuneSteps));
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (groups)");
+    float best = 1e30f;
+    int best_g = 1;
+    for (int c = 0; c < 3 && cand[c] <= Bt; ++c) {
+        p.tune_group_us[c] = t_min[c];
+        if (t_min[c] < best * 0.97f) {  // prefer fewer streams unless 3 % faster
+            best = t_min[c];
+            best_g = cand[c];
+        }
+    }
     p.prop_groups = best_g;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_group_cache[key] = best_g;
@@ -511,7 +531,9 @@ ts_status autotune_fused(Plan& p)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (fused)");
     ts_status stt = TS_OK;
-    for (int c = 0; c < 2 && stt == TS_OK; ++c) {
+    p.tune_fused_us[0] = p.tune_fused_us[1] = 1e30f;
+    for (int rd = 0; rd < kTuneRounds * 2 && stt == TS_OK; ++rd) {  // interleaved rounds, as above
+        const int c = rd % 2;
         p.fused = c == 1;
         auto once = [&]() { return propagate_groups(p, U, Bt, nullptr, ph, Bt, 0, 0, 0, nullptr, nullptr, nullptr); };
         for (int w = 0; w < 2 && stt == TS_OK; ++w) stt = once();
@@ -521,7 +543,7 @@ ts_status autotune_fused(Plan& p)
         if (stt == TS_OK) stt = cuda_check(cudaEventSynchronize(e1), "autotune (fused)");
         float ms = 0.0f;
         if (stt == TS_OK) stt = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "autotune (fused)");
-        p.tune_fused_us[c] = ms * 1000.0f / 5.0f;
+        if (stt == TS_OK) p.tune_fused_us[c] = std::min(p.tune_fused_us[c], ms * 1000.0f / 5.0f);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
