@@ -680,6 +680,17 @@ def test_tuning_candidate_table():
     timed = [c[3] for c in cands if c[3] > 0]
     if timed:  # not a cached result
         assert chosen[0][3] == min(timed)
+    # field groups: fewer streams unless at least 3 % faster (timings are each candidate's fastest round)
+    us = t[4]
+    if all(u > 0 for u in us):
+        best, best_g = np.float32(np.inf), 1
+        for g, u in zip((1, 2, 4), us):
+            if np.float32(u) < best * np.float32(0.97):  # the library's float comparison
+                best, best_g = np.float32(u), g
+        assert t[3] == best_g
+    fused, us_pass, us_fused = plan.tuning_fused()
+    if us_pass > 0 and us_fused > 0:
+        assert fused == (us_fused < us_pass)
 
 
 @pytest.mark.parametrize("groups", [2, 4])
