@@ -1,0 +1,111 @@
+"""Full-size parity for the Monte Carlo (config 2) and differentiable-path (config 5) workloads, in
+the launch configuration their benchmarks time (one plan for the whole batch, autotuned passes and
+field groups, screens synthesised or regenerated from the seed), on sampled outputs the FP64 oracle
+computes one by one.  Tolerances as in the other parity tests: 1e-5 relative L2 for fields (2e-5
+for intensities, whose rounding doubles), 1e-4 for gradients."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker keeps these off CPU runs
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2604_07248_gb300 as ts  # noqa: E402
+from paper_2604_07248_gb300 import workloads as W  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) else np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_config2_full_chunk_sampled_beams():
+    # one Monte Carlo step of the benchmark: 32 realizations of 10 screens with 3-level subharmonics
+    # synthesised as phasors, a plane wave and a 2 cm Gaussian through each realization's screens
+    # (64 fields, intensity and beam sums only); fields 0, 1, 42 and 63 against the oracle
+    cn2 = W.config2_cn2()[5]
+    wl = W.config2(cn2)
+    N, S, Rc = wl.N, wl.S, 32
+    B = 2 * Rc
+    plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, sh_levels=3, max_batch=B)
+    plan.set_sources(wl.w0)
+    r0 = 5 * 1000 + 3 * Rc
+    ph = torch.zeros((Rc, S, N, N), dtype=torch.complex64, device=DEV)
+    plan.make_screens(None, wl.seed, real_base=r0, n_real=Rc, phasor=ph)
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    sums = torch.zeros((B, 2), dtype=torch.float64, device=DEV)
+    plan.propagate(U, B, phasor=ph, phi_group=2,
+                   flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY | ts.TS_PROP_NO_FIELD, intensity=I, beam_sums=sums)
+    torch.cuda.synchronize()
+    plan.device_status()
+    md = O.medium(W.LAMBDA, N, wl.dx, l0=W.L0_INNER, L0=W.L0_OUTER)
+    for b in (0, 1, 42, 63):
+        r = r0 + b // 2
+        phis = np.stack([O.make_screen(md, cn2, wl.dz[s], 3, wl.seed, s, r) for s in range(S)])
+        src = np.ones((N, N), complex) if b % 2 == 0 else O.source_gaussian(N, wl.dx, wl.w0[1])
+        Iref = np.abs(O.propagate(md, wl.dz, phis, src)) ** 2
+        assert rel_l2(I[b].cpu().numpy(), Iref) < 2e-5, (b, rel_l2(I[b].cpu().numpy(), Iref))
+        sI, sR = O.beam_sums(N, wl.dx, Iref)
+        assert abs(sums[b, 0].item() / sI - 1) < 2e-5 and abs(sums[b, 1].item() / sR - 1) < 2e-5
+
+
+def test_config5_full_batch_sampled_beams():
+    # the differentiable path of the benchmark: 64 beams in one plan, screens regenerated from the
+    # seed at the benchmark's realization base, the two-mask receiver and its adjoint, then the
+    # adjoint path; beams 0, 37 and 63 (fields, intensities, input gradients) against the oracle.
+    # The squared-error loss stands in for the benchmark's MAE here: per pixel the MAE gradient is a
+    # sign, which FP32 and FP64 may take differently where I is within rounding of the target.
+    wl = W.config5()
+    N, S, B, AP = wl.N, wl.S, wl.realizations, wl.extra["aperture"]
+    plan = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, wl.cn2, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
+    plan.set_sources(wl.w0)
+    vac = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, [0.0] * S, max_batch=1)
+    vac.set_sources(wl.w0)
+    th1n, th2n = W.config5_masks(N, wl.seed)
+    th1, th2 = torch.from_numpy(th1n).to(DEV), torch.from_numpy(th2n).to(DEV)
+    Uv = torch.zeros((1, N, N), dtype=torch.complex64, device=DEV)
+    vac.propagate(Uv, 1, flags=ts.TS_PROP_SOURCE)
+    z = torch.zeros((N, N), dtype=torch.float32, device=DEV)
+    Iv = torch.zeros((1, N, N), dtype=torch.float32, device=DEV)
+    vac.d2nn_forward(Uv, 1, z, z, AP, z, 1, torch.zeros((3, 1, N, N), dtype=torch.complex64, device=DEV), Iv,
+                     torch.zeros(1, dtype=torch.float64, device=DEV))
+    Iref = Iv[0].contiguous()
+    real = 7 * B
+    U = torch.zeros((B, N, N), dtype=torch.complex64, device=DEV)
+    plan.propagate(U, B, flags=ts.TS_PROP_SOURCE, seed=wl.seed, real_base=real)
+    Uout = U.clone()
+    ws = torch.zeros((3, B, N, N), dtype=torch.complex64, device=DEV)
+    I = torch.zeros((B, N, N), dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    g1, g2 = torch.zeros_like(z), torch.zeros_like(z)
+    gU = torch.zeros_like(U)
+    plan.d2nn_forward(U, B, th1, th2, AP, Iref, 1, ws, I, loss)
+    plan.d2nn_backward(B, th1, th2, AP, Iref, 1, ws, I, g1, g2, gU)
+    plan.propagate_backward(gU, B, seed=wl.seed, real_base=real)
+    torch.cuda.synchronize()
+    plan.device_status()
+
+    md = O.medium(W.LAMBDA, N, wl.dx, l0=W.L0_INNER, L0=W.L0_OUTER)
+    A = O.aperture(N, wl.dx, AP)
+    Iref_o = np.abs(A * O.propagate(md, wl.dz, None, O.source_gaussian(N, wl.dx, wl.w0[0]))) ** 2
+    assert rel_l2(Iref.cpu().numpy(), Iref_o) < 1e-5
+    t1o, t2o = th1n.astype(np.float64), th2n.astype(np.float64)
+    for b in (0, 37, 63):
+        phis = np.stack([O.make_screen(md, wl.cn2[s], wl.dz[s], 0, wl.seed, s, real + b) for s in range(S)])
+        Ub = O.propagate(md, wl.dz, phis, O.source_gaussian(N, wl.dx, wl.w0[0]))
+        assert rel_l2(Uout[b].cpu().numpy(), Ub) < 1e-5, (b, rel_l2(Uout[b].cpu().numpy(), Ub))
+        Ib, Z1, W2, V = O.d2nn_forward(A, t1o, t2o, Ub)
+        assert rel_l2(I[b].cpu().numpy(), Ib) < 2e-5
+        _, dLdI = O.intensity_loss(Ib, Iref_o, 1, B * N * N)
+        gUb = O.d2nn_backward(A, t1o, t2o, Z1, W2, V, dLdI, np.zeros((N, N)), np.zeros((N, N)))
+        gin = O.propagate_adjoint(md, wl.dz, phis, gUb)
+        assert rel_l2(gU[b].cpu().numpy(), gin) < 1e-4, (b, rel_l2(gU[b].cpu().numpy(), gin))
+    plan.close()
+    vac.close()
