@@ -1,7 +1,7 @@
-"""Full-size parity for the Monte Carlo (config 2) and differentiable-path (config 5) workloads, in
-the launch configuration their benchmarks time (one plan for the whole batch, autotuned passes and
-field groups, screens synthesised or regenerated from the seed), on sampled outputs the FP64 oracle
-computes one by one.  Tolerances as in the other parity tests: 1e-5 relative L2 for fields (2e-5
+"""Full-size parity for the Monte Carlo (config 2), uneven-batch (config 4) and differentiable-path
+(config 5) workloads, in the launch configuration their benchmarks time (the whole batch in one plan
+or one persistent launch, autotuned passes and field groups, screens synthesised or regenerated from
+the seed), on sampled outputs the FP64 oracle computes one by one and on energy conservation.  Tolerances as in the other parity tests: 1e-5 relative L2 for fields (2e-5
 for intensities, whose rounding doubles), 1e-4 for gradients."""
 import numpy as np
 import pytest
@@ -109,3 +109,41 @@ def test_config5_full_batch_sampled_beams():
         assert rel_l2(gU[b].cpu().numpy(), gin) < 1e-4, (b, rel_l2(gU[b].cpu().numpy(), gin))
     plan.close()
     vac.close()
+
+
+def test_config4_full_uneven_batch():
+    # the benchmark's 64-instance uneven batch (N = 256 ... 2048, 4 to 20 screens, one persistent
+    # launch): every instance conserves the source's energy (the split step is unitary: |H| = 1 below
+    # the evanescent cutoff, which these grids never reach, and |exp(i phi)| = 1), and the first two
+    # instances at N = 256 and the first at N = 512 match the oracle field by field
+    spec = W.config4_instances()
+    seed = W.SEED_BASE + 4
+    plans, fields, insts = [], [], []
+    for i, d in enumerate(spec):
+        p = ts.Plan(W.LAMBDA, d["N"], d["dx"], [d["L"] / d["S"]] * d["S"], [d["cn2"]] * d["S"], l0=W.L0_INNER,
+                    L0=W.L0_OUTER, max_batch=1)
+        p.set_sources([d["w0"]])
+        f = torch.zeros((d["N"], d["N"]), dtype=torch.complex64, device=DEV)
+        plans.append(p)
+        fields.append(f)
+        insts.append(dict(plan=p, field=f, phasor=None, seed=seed, real=i, source=True))
+    batch = ts.Batch(insts, timeout_s=10.0)
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for i, d in enumerate(spec):
+        e_out = float((fields[i].to(torch.complex128).abs() ** 2).sum().item())
+        e_in = float(np.sum(np.abs(O.source_gaussian(d["N"], d["dx"], d["w0"])) ** 2))
+        assert abs(e_out / e_in - 1) < 2e-5, (i, d["N"], d["S"], e_out / e_in)
+    n256 = [i for i, d in enumerate(spec) if d["N"] == 256][:2]
+    n512 = [i for i, d in enumerate(spec) if d["N"] == 512][:1]
+    for i in n256 + n512:
+        d = spec[i]
+        N, S, dz = d["N"], d["S"], d["L"] / d["S"]
+        md = O.medium(W.LAMBDA, N, d["dx"], l0=W.L0_INNER, L0=W.L0_OUTER)
+        phis = np.stack([O.make_screen(md, d["cn2"], dz, 0, seed, s, i) for s in range(S)])
+        ref = O.propagate(md, [dz] * S, phis, O.source_gaussian(N, d["dx"], d["w0"]))
+        assert rel_l2(fields[i].cpu().numpy(), ref) < 1e-5, (i, rel_l2(fields[i].cpu().numpy(), ref))
+    batch.close()
+    for p in plans:
+        p.close()
