@@ -139,6 +139,25 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _need(t, name: str, dtype, numel: int):
+    """Checks a buffer before its raw pointer crosses the C ABI: a CUDA tensor of `dtype` (a torch
+    dtype name, or a tuple of names any of which will do) holding at least `numel` elements.  The library receives only pointers and sizes, so
+    an undersized or mistyped buffer would be read or written out of bounds on the device; here it
+    raises on the host instead.  None passes (optional buffers)."""
+    if t is None:
+        return
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    names = (dtype,) if isinstance(dtype, str) else tuple(dtype)
+    if not any(t.dtype == getattr(torch, nm, None) for nm in names):
+        raise TypeError(f"{name} must be torch.{' or torch.'.join(names)}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {numel}")
+
+
 def _stream(stream) -> int | None:
     if stream is None:
         import torch
@@ -153,7 +172,10 @@ def max_step(lam, N, dx, n0=1.0) -> float:
 
 def adam_step(param, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     """One Adam step on device float32 tensors (see ts_adam_step); t >= 1."""
-    _check(load().ts_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()), float(lr), float(beta1),
+    n = int(param.numel())
+    for t_, nm in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t_, nm, "float32", n)
+    _check(load().ts_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, float(lr), float(beta1),
                                float(beta2), float(eps), int(t), _stream(stream)), "ts_adam_step")
 
 
@@ -203,6 +225,8 @@ def place_screens(prof_z, prof_cn2, lam, N, dx, L, rytov_limit, init_bounds=None
 def philox4x32_10(ctr, key0, key1, out, stream=None):
     """Philox4x32-10 words of n counters (ctr, out: device uint32 tensors of 4n words)."""
     n = ctr.numel() // 4
+    _need(ctr, "ctr", ("int32", "uint32"), 4 * n)  # 32-bit words
+    _need(out, "out", ("int32", "uint32"), 4 * n)
     _check(load().ts_philox4x32_10(_ptr(ctr), int(key0), int(key1), n, _ptr(out), _stream(stream)),
            "ts_philox4x32_10")
 
@@ -212,6 +236,7 @@ def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0
     ts_make_screen_noalloc in include/turbscreen.h."""
     L0v = float(L0) if (L0 is not None and math.isfinite(L0)) else 0.0
     med = Medium(float(lam), float(n0), float(l0), L0v)
+    _need(phi, "phi", "float32", int(N) * int(N))
     _check(load().ts_make_screen_noalloc(C.byref(med), C.byref(Grid(int(N), float(dx))), float(dz), float(cn2),
                                          int(seed), int(screen), int(real), _ptr(phi), _stream(stream)),
            "ts_make_screen_noalloc")
@@ -223,6 +248,9 @@ def tc_dft32(x, X, sign=-1, layout=0, err=None, timeout_s=1.0, stream=None):
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device=x.device)
     nvec = x.numel() // 32
+    _need(x, "x", "complex64", 32 * nvec)
+    _need(X, "X", "complex64", 32 * nvec)
+    _need(err, "err", "int32", 1)
     _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), int(layout), float(timeout_s), _ptr(err),
                               _stream(stream)),
            "ts_tc_dft32")
@@ -338,43 +366,91 @@ class Plan:
         w = (C.c_double * len(w0))(*[float(x) for x in w0])
         _check(load().ts_plan_set_sources(self._h, len(w0), w), "ts_plan_set_sources")
 
+    def _n2(self) -> int:
+        return self.N * self.N
+
     def make_sources(self, field, B, stream=None):
+        _need(field, "field", "complex64", int(B) * self._n2())
         _check(load().ts_make_sources(self._h, _ptr(field), int(B), _stream(stream)), "ts_make_sources")
 
     def make_screens(self, phi, seed, real_base=0, n_real=1, phasor=None, stream=None):
+        n = int(n_real) * self.S * self._n2()
+        _need(phi, "phi", "float32", n)
+        _need(phasor, "phasor", "complex64", n)
         _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _ptr(phasor),
                                       _stream(stream)), "ts_make_screens")
 
     def evolve_screens(self, spec, phi, seed, t, alpha, real=0, vx=0.0, vy=0.0, T=0.0, sh_state=None, phasor=None,
                        stream=None):
+        n = self.S * self._n2()
+        _need(spec, "spec", "complex64", n)
+        _need(phi, "phi", "float32", n)
+        _need(phasor, "phasor", "complex64", n)
+        _need(sh_state, "sh_state", "complex128", self.S * 27)
         _check(load().ts_evolve_screens(self._h, int(seed), int(real), int(t), float(alpha), float(vx), float(vy),
                                         float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _ptr(phasor),
                                         _stream(stream)), "ts_evolve_screens")
 
     def propagate(self, field, B, phi=None, phi_group=1, flags=0, seed=0, real_base=0, intensity=None,
                   beam_sums=None, phasor=None, stream=None):
+        self._need_path(field, "field", B, phi, phasor, phi_group)
+        _need(intensity, "intensity", "float32", int(B) * self._n2())
+        _need(beam_sums, "beam_sums", "float64", 2 * int(B))
         _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), _ptr(phasor), int(phi_group), int(flags),
                                    int(seed), int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream)),
                "ts_propagate")
 
+    def _need_path(self, field, name, B, phi, phasor, phi_group):
+        """The field [B][N][N] and the screen sets [ceil(B / phi_group)][S][N][N] of a propagation."""
+        B, g = int(B), max(1, int(phi_group))
+        _need(field, name, "complex64", B * self._n2())
+        n = -(-B // g) * self.S * self._n2()
+        _need(phi, "phi", "float32", n)
+        _need(phasor, "phasor", "complex64", n)
+
     def propagate_backward(self, grad, B, phi=None, phi_group=1, seed=0, real_base=0, phasor=None, stream=None):
+        self._need_path(grad, "grad", B, phi, phasor, phi_group)
         _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), _ptr(phasor), int(phi_group),
                                             int(seed), int(real_base), _stream(stream)), "ts_propagate_backward")
 
     def moments_accumulate(self, intensity, B, n_groups, count, mean, m2, stream=None):
+        _need(intensity, "intensity", "float32", int(B) * self._n2())
+        _need(mean, "mean", "float64", int(n_groups) * self._n2())
+        _need(m2, "m2", "float64", int(n_groups) * self._n2())
         _check(load().ts_moments_accumulate(self._h, _ptr(intensity), int(B), int(n_groups), int(count), _ptr(mean),
                                             _ptr(m2), _stream(stream)), "ts_moments_accumulate")
 
     def moments_finalize(self, mean, m2, n_groups, count, si_map=None, si_mean=None, si_center=None, stream=None):
+        n = int(n_groups) * self._n2()
+        _need(mean, "mean", "float64", n)
+        _need(m2, "m2", "float64", n)
+        _need(si_map, "si_map", "float64", n)
+        _need(si_mean, "si_mean", "float64", int(n_groups))
+        _need(si_center, "si_center", "float64", int(n_groups))
         _check(load().ts_moments_finalize(self._h, _ptr(mean), _ptr(m2), int(n_groups), int(count), _ptr(si_map),
                                           _ptr(si_mean), _ptr(si_center), _stream(stream)), "ts_moments_finalize")
 
+    def _need_d2nn(self, B, th1, th2, Iref, ws, intensity):
+        n2, B = self._n2(), int(B)
+        _need(th1, "th1", "float32", n2)
+        _need(th2, "th2", "float32", n2)
+        _need(Iref, "Iref", "float32", n2)
+        _need(ws, "ws", "complex64", 3 * B * n2)
+        _need(intensity, "intensity", "float32", B * n2)
+
     def d2nn_forward(self, U, B, th1, th2, aperture, Iref, kind, ws, intensity, loss, stream=None):
+        _need(U, "U", "complex64", int(B) * self._n2())
+        self._need_d2nn(B, th1, th2, Iref, ws, intensity)
+        _need(loss, "loss", "float64", 1)
         _check(load().ts_d2nn_forward(self._h, _ptr(U), int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref),
                                       int(kind), _ptr(ws), _ptr(intensity), _ptr(loss), _stream(stream)),
                "ts_d2nn_forward")
 
     def d2nn_backward(self, B, th1, th2, aperture, Iref, kind, ws, intensity, g_th1, g_th2, gU, stream=None):
+        self._need_d2nn(B, th1, th2, Iref, ws, intensity)
+        _need(g_th1, "g_th1", "float32", self._n2())
+        _need(g_th2, "g_th2", "float32", self._n2())
+        _need(gU, "gU", "complex64", int(B) * self._n2())
         _check(load().ts_d2nn_backward(self._h, int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref), int(kind),
                                        _ptr(ws), _ptr(intensity), _ptr(g_th1), _ptr(g_th2), _ptr(gU),
                                        _stream(stream)), "ts_d2nn_backward")
@@ -387,7 +463,10 @@ class Batch:
         """instances: list of dicts with keys plan, field, phasor (or None), seed, real, source."""
         arr = (BatchInstance * len(instances))()
         for i, d in enumerate(instances):
-            arr[i].plan = d["plan"].handle.value
+            pl = d["plan"]
+            _need(d["field"], f"instances[{i}].field", "complex64", pl.N * pl.N)
+            _need(d.get("phasor"), f"instances[{i}].phasor", "complex64", pl.S * pl.N * pl.N)
+            arr[i].plan = pl.handle.value
             arr[i].field = _ptr(d["field"])
             arr[i].phasor = _ptr(d.get("phasor"))
             arr[i].seed = int(d.get("seed", 0))

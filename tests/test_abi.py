@@ -91,3 +91,21 @@ def test_status_strings_and_null_handling():
     assert lib.ts_make_screens(None, 0, 0, 1, None, None, None) == 1
     assert lib.ts_propagate(None, None, 1, None, None, 1, 0, 0, 0, None, None, None) == 1
     assert b"need" in lib.ts_last_error()
+
+
+def test_buffers_are_checked_before_their_pointers_cross_the_abi():
+    # the C ABI takes raw pointers and sizes: the binding refuses a buffer of the wrong dtype, on the
+    # wrong device or too small for the call, on the host, before anything is launched
+    torch = pytest.importorskip("torch")
+    bd._need(None, "optional", "float32", 10)  # optional buffers pass
+    with pytest.raises(TypeError):
+        bd._need(np.zeros(10, np.float32), "x", "float32", 10)
+    with pytest.raises(TypeError):
+        bd._need(torch.zeros(10, dtype=torch.float64), "x", "float32", 10)
+    with pytest.raises(ValueError, match="CUDA"):
+        bd._need(torch.zeros(10, dtype=torch.float32), "x", "float32", 10)
+    with pytest.raises(TypeError):
+        bd._need(torch.zeros(8, dtype=torch.int64), "ctr", ("int32", "uint32"), 8)
+    if torch.cuda.is_available():  # pragma: no cover - the size check itself, on a CUDA tensor
+        with pytest.raises(ValueError, match="needs 11"):
+            bd._need(torch.zeros(10, dtype=torch.float32, device="cuda"), "x", "float32", 11)

@@ -116,7 +116,7 @@ def test_ar_with_alpha_one_is_a_pure_translation():
 
 def test_empty_and_oversized_requests_are_rejected():
     plan = ts.Plan(LAM, 128, 2e-3, [100.0], [1e-15], max_batch=2)
-    U = torch.zeros((2, 128, 128), dtype=torch.complex64, device=DEV)
+    U = torch.zeros((3, 128, 128), dtype=torch.complex64, device=DEV)  # room for B = 3: the library refuses it
     for B in (0, -1, 3):
         with pytest.raises(ts.TsError):
             plan.propagate(U, B)
@@ -125,3 +125,33 @@ def test_empty_and_oversized_requests_are_rejected():
         plan.make_screens(phi, 1, n_real=0)
     with pytest.raises(ts.TsError):
         plan.propagate(U, 1, phi_group=0)
+
+
+def test_undersized_or_mistyped_buffers_are_refused_on_the_host():
+    # the binding checks every buffer against the call's sizes before its pointer reaches the
+    # library, so a short field, a missing screen set or a wrong dtype never reaches a kernel
+    N, S = 256, 2
+    plan = ts.Plan(LAM, N, 1e-3, [100.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=4)
+    U = torch.zeros((3, N, N), dtype=torch.complex64, device=DEV)
+    with pytest.raises(ValueError, match="field"):
+        plan.propagate(U, 4, seed=1)  # 3 of the 4 fields
+    one = torch.zeros((1, 1, N, N), dtype=torch.complex64, device=DEV)
+    with pytest.raises(ValueError, match="phasor"):
+        plan.propagate(U, 3, phasor=one, phi_group=3)  # 1 of the S = 2 screens of the set
+    with pytest.raises(TypeError, match="field"):
+        plan.propagate(U.to(torch.complex128), 3, seed=1)
+    with pytest.raises(ValueError, match="spec"):
+        plan.evolve_screens(torch.zeros((1, N, N), dtype=torch.complex64, device=DEV), None, 1, 0, 0.99,
+                            phasor=torch.zeros((S, N, N), dtype=torch.complex64, device=DEV))
+    with pytest.raises(ValueError, match="mean"):
+        plan.moments_accumulate(torch.zeros((4, N, N), dtype=torch.float32, device=DEV), 4, 2, 0,
+                                torch.zeros((1, N, N), dtype=torch.float64, device=DEV),
+                                torch.zeros((2, N, N), dtype=torch.float64, device=DEV))
+    with pytest.raises(ValueError, match="grad"):
+        plan.propagate_backward(U, 4, seed=1)
+    # nothing was launched: the plan works as before
+    plan.propagate(U, 3, seed=1)
+    torch.cuda.synchronize()
+    plan.device_status()
+    assert bool(torch.isfinite(torch.view_as_real(U)).all())
+    plan.close()
