@@ -109,3 +109,36 @@ def test_buffers_are_checked_before_their_pointers_cross_the_abi():
     if torch.cuda.is_available():  # pragma: no cover - the size check itself, on a CUDA tensor
         with pytest.raises(ValueError, match="needs 11"):
             bd._need(torch.zeros(10, dtype=torch.float32, device="cuda"), "x", "float32", 11)
+
+
+def test_every_plan_entry_point_refuses_a_null_handle_without_a_gpu():
+    # the boundary's error convention: a NULL plan or batch handle is TS_ERR_INVALID_ARG, returned
+    # before any CUDA call (so this runs on a machine without a GPU); destroying NULL is a no-op
+    lib = bd.load()
+    N = None
+    calls = {
+        "ts_plan_device_status": (N,),
+        "ts_plan_set_loss_scale": (N, 1.0),
+        "ts_plan_tuning": (N,) + (None,) * 9,
+        "ts_plan_tuning_candidates": (N, 0, None, None, None, None, None),
+        "ts_plan_tuning_fused": (N, None, None, None),
+        "ts_plan_set_sources": (N, 1, None),
+        "ts_make_sources": (N, None, 1, None),
+        "ts_make_screens": (N, 1, 0, 1, None, None, None),
+        "ts_evolve_screens": (N, 1, 0, 0, 0.9, 0.0, 0.0, 0.0, None, None, None, None, None),
+        "ts_propagate": (N, None, 1, None, None, 1, 0, 0, 0, None, None, None),
+        "ts_propagate_backward": (N, None, 1, None, None, 1, 0, 0, None),
+        "ts_moments_accumulate": (N, None, 1, 1, 0, None, None, None),
+        "ts_moments_finalize": (N, None, None, 1, 1, None, None, None, None),
+        "ts_d2nn_forward": (N, None, 1, None, None, 0.3, None, 0, None, None, None, None),
+        "ts_d2nn_backward": (N, 1, None, None, 0.3, None, 0, None, None, None, None, None, None),
+        "ts_plan_timing": (N, 1, 4),
+        "ts_plan_timing_read": (N, 0, None, None),
+        "ts_batch_run": (N, None),
+        "ts_batch_status": (N, None),
+        "ts_batch_info": (N, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == 1, name  # TS_ERR_INVALID_ARG
+    assert lib.ts_plan_destroy(None) == bd.TS_OK and lib.ts_batch_destroy(None) == bd.TS_OK
+    assert lib.ts_plan_device_bytes(None) == 0
