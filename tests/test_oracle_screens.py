@@ -107,12 +107,122 @@ def test_screen_structure_function_matches_model(sh):
     for i, lag in enumerate(lags):
         ex = _exact_structure_function(md, cn2, dz, sh, lag)
         assert abs(D[i] / ex - 1) < 0.08, (lag, D[i] / ex)
-    # the 3-level subharmonics recover most of the large-separation deficit (Sec. 2.2, Fig. 2)
-    if sh:
-        r0 = r0_of(cn2, dz)
-        th = lambda lag: 6.88 * (lag * dx / r0) ** (5 / 3)
-        assert _exact_structure_function(md, cn2, dz, 3, 16) / th(16) > 0.75
-        assert _exact_structure_function(md, cn2, dz, 0, 16) / th(16) < 0.5
+
+
+def _ring_integral(md, cn2, dz, h, ni, mi):
+    """Integral of the phase PSD over the cell [ni - 1/2, ni + 1/2] x [mi - 1/2, mi + 1/2] (units of h),
+    by adaptive 2-D quadrature of phase_psd alone."""
+    f = lambda ky, kx: O.phase_psd(md, cn2, dz, kx * kx + ky * ky)
+    return integrate.dblquad(f, (ni - 0.5) * h, (ni + 0.5) * h, (mi - 0.5) * h, (mi + 0.5) * h,
+                             epsabs=0, epsrel=1e-9)[0]
+
+
+def test_subharmonic_amplitudes_carry_the_psd_of_their_cells():
+    # Two-sided pin of the subharmonic amplitudes (Eq. 2): cell (n', m') of level p stands for the
+    # square of side dk / 3^p centred on (n', m') dk / 3^p, so its variance b^2 must be the phase PSD
+    # integrated over that cell.  With an outer scale much smaller than the grid (kappa0 = 2 pi / L0
+    # well above dk) the PSD is smooth across every subharmonic cell and the midpoint value times the
+    # cell area equals the integral to O((cell / kappa0)^2): a factor 3^p or sqrt(3) in any level's
+    # amplitude, or a frequency at the wrong scale, is off by far more than the tolerance.
+    N, dx, cn2, dz = 64, 2e-3, 1e-14, 100.0
+    md = O.medium(LAM, N, dx, l0=0.0, L0=0.02)
+    dk = 2 * np.pi / (N * dx)
+    b = O.sh_amplitude(md, cn2, dz)
+    for p in range(1, 4):
+        h = dk / 3 ** p
+        assert b[p - 1, 4] == 0.0
+        for q in range(9):
+            mi, ni = q // 3 - 1, q % 3 - 1
+            if mi == 0 and ni == 0:
+                continue
+            ratio = b[p - 1, q] ** 2 / _ring_integral(md, cn2, dz, h, ni, mi)
+            assert abs(ratio - 1) < 2e-3 * 9.0 ** (1 - p) + 1e-5, (p, q, ratio)
+
+
+def test_subharmonic_levels_replicate_the_first_grid_ring():
+    # For the pure power law (l0 = 0, L0 = inf) the PSD is self-similar, so each subharmonic level is a
+    # 1/3^p scale copy of the FFT grid's first ring of 8 bins around DC: the fraction of the ring's PSD
+    # integral that the 8 point samples carry is the same number for the grid (amplitudes from
+    # psd_amplitude, pinned by the PSD-recovery expectation) and for every level.  The number itself
+    # (about 0.60: point samples under-weight the kappa^(-11/3) rise toward the origin) is the known
+    # low-frequency deficit of the method; a wrong 3^p scaling of an amplitude changes it by 9^p.
+    N, dx, cn2, dz = 64, 2e-3, 1e-14, 100.0
+    md = O.medium(LAM, N, dx, l0=0.0, L0=np.inf)
+    dk = 2 * np.pi / (N * dx)
+    s = O.psd_amplitude(md, cn2, dz)
+    ring = [(ni, mi) for mi in (-1, 0, 1) for ni in (-1, 0, 1) if (ni, mi) != (0, 0)]
+    grid = sum(s[mi % N, ni % N] ** 2 for ni, mi in ring) / sum(_ring_integral(md, cn2, dz, dk, ni, mi) for ni, mi in ring)
+    assert 0.55 < grid < 0.65
+    b = O.sh_amplitude(md, cn2, dz)
+    for p in range(1, 4):
+        h = dk / 3 ** p
+        lev = sum(b[p - 1, q] ** 2 for q in range(9)) / sum(_ring_integral(md, cn2, dz, h, ni, mi) for ni, mi in ring)
+        assert abs(lev / grid - 1) < 1e-6, (p, lev, grid)
+
+
+def test_subharmonic_screens_have_the_structure_function_of_their_coefficients():
+    # The subharmonic part of an oracle screen (same seed with and without subharmonics: the grid noise
+    # is drawn from its own counters) is a sum of 24 random plane waves, so its expected structure
+    # function is sum_q 2 b_q^2 (1 - cos(kappa_q . r)) (Re and Im of the noise each N(0,1)).  The Monte
+    # Carlo average over the screens' pixels must reach it: pins the noise normalisation and the
+    # frequencies (n', m') dk / 3^p that the screen synthesis places the amplitudes at.
+    N, dx, cn2, dz, M = 32, 2e-3, 1e-14, 100.0, 2000
+    md = O.medium(LAM, N, dx, l0=0.0, L0=np.inf)
+    dk = 2 * np.pi / (N * dx)
+    lags = (2, 8, 31)
+    vals = np.zeros((M, len(lags)))
+    for sidx in range(M):
+        d = O.make_screen(md, cn2, dz, 3, 11, sidx, 0) - O.make_screen(md, cn2, dz, 0, 11, sidx, 0)
+        for i, lag in enumerate(lags):
+            vals[sidx, i] = 0.5 * (np.mean((d[:, lag:] - d[:, :-lag]) ** 2) + np.mean((d[lag:] - d[:-lag]) ** 2))
+    b = O.sh_amplitude(md, cn2, dz)
+    for i, lag in enumerate(lags):
+        r = lag * dx
+        ex = 0.0
+        for p in range(1, 4):
+            for q in range(9):
+                kx, ky = (q % 3 - 1) * dk / 3 ** p, (q // 3 - 1) * dk / 3 ** p
+                ex += b[p - 1, q] ** 2 * (2 - np.cos(kx * r) - np.cos(ky * r))
+        mc, se = vals[:, i].mean(), vals[:, i].std() / np.sqrt(M)
+        assert abs(mc - ex) < 5 * se, (lag, mc / ex, se / ex)
+
+
+def test_kolmogorov_structure_function_with_subharmonics():
+    # Survey pin P5 (Eq. 2-3, S18): l0 = 0, L0 = inf, N = 256, 3-level subharmonics.  (1) The oracle's
+    # screens reach the exact expectation of the discrete model at every lag.  (2) Against
+    # 6.88 (r / r0)^(5/3) for 2 dx <= r <= N dx / 8 the model lies between 0.75 and 0.95: the grid
+    # square itself holds >= 0.98 of D(r) (polar quadrature below), and the remaining deficit is the
+    # point sampling of the kappa^(-11/3) spectrum in the cells bordering the origin (each level carries
+    # 0.60 of its ring's PSD, the test above), which grows toward large r (0.89 at r = 2 dx, 0.77 at
+    # N dx / 8 for this grid).  (3) Without subharmonics the large-r deficit is more than twice as deep.
+    N, dx, cn2, dz, M = 256, 2e-3, 1e-14, 100.0, 240
+    md = O.medium(LAM, N, dx, l0=0.0, L0=np.inf)
+    r0 = r0_of(cn2, dz)
+    lags = (2, 4, 8, 16, 32)
+    vals = np.zeros((M, len(lags)))
+    for sidx in range(M):
+        phi = O.make_screen(md, cn2, dz, 3, 2604, sidx, 0)
+        for i, lag in enumerate(lags):
+            vals[sidx, i] = 0.5 * (np.mean((phi[:, lag:] - phi[:, :-lag]) ** 2) + np.mean((phi[lag:] - phi[:-lag]) ** 2))
+    K = np.pi / dx
+    for i, lag in enumerate(lags):
+        r = lag * dx
+        th = 6.88 * (r / r0) ** (5 / 3)
+        model = _exact_structure_function(md, cn2, dz, 3, lag)
+        mc, se = vals[:, i].mean(), vals[:, i].std() / np.sqrt(M)
+        assert abs(mc - model) < 5 * se, (lag, mc / model, se / model)
+        assert 0.75 < model / th < 0.95, (lag, model / th)
+        if lag in (2, 32):
+            # fraction of D(r) inside the grid square |kx|, |ky| < pi / dx, in polar coordinates
+            def wedge(t):
+                g = lambda k: 2 * O.phase_psd(md, cn2, dz, k * k) * (
+                    1 - 0.5 * (np.cos(k * np.cos(t) * r) + np.cos(k * np.sin(t) * r))) * k
+                pts = [0.0, 1 / r, 10 / r, K / np.cos(t)]
+                return sum(integrate.quad(g, a, c, limit=400)[0] for a, c in zip(pts[:-1], pts[1:]))
+            inside = 8 * integrate.quad(wedge, 0, np.pi / 4, limit=100)[0]
+            assert 0.98 < inside / th < 1.01, (lag, inside / th)
+    big = _exact_structure_function(md, cn2, dz, 0, 32) / (6.88 * (32 * dx / r0) ** (5 / 3))
+    assert big < 0.5 and 1 - big > 2 * (1 - _exact_structure_function(md, cn2, dz, 3, 32) / (6.88 * (32 * dx / r0) ** (5 / 3)))
 
 
 def test_subharmonic_screen_separable_form():
