@@ -24,6 +24,11 @@
  *     host before any launch; a failing check launches nothing.  One plan must not be used
  *     concurrently from two host threads or two unordered streams (it owns one workspace).
  *   - on error a call returns a non-zero ts_status and ts_last_error() gives a one-line detail.
+ *   - a plan (and a batch) belongs to the CUDA device that was current when it was created; every
+ *     call on it must be made with that device current and with buffers on that device.  A call
+ *     made while another device is current returns TS_ERR_INVALID_ARG and launches nothing (the
+ *     library cannot tell on which device a raw pointer lives, so matching the buffers is the
+ *     caller's part; the Python binding checks them).
  */
 #ifndef TURBSCREEN_H
 #define TURBSCREEN_H
@@ -118,7 +123,11 @@ double ts_power_law_constant(double alpha);
  * (and clears the flag) if a bounded device wait of its passes ran out of its one-second budget since
  * the last call -- a tensor-core pass (TS_PLAN_SPLIT_BF16) waiting for its MMAs, or a prefetching
  * pass (column / row variant 2) waiting for its TMA copy; the pass then stopped early and its output
- * is incomplete -- else TS_OK. */
+ * is incomplete -- else TS_OK.  A CTA (or warp) whose wait ran out waits once more, again bounded, for
+ * its own copy in flight before it exits; if that second wait also runs out, the copy engine has not
+ * delivered within two seconds and may still write into shared memory that a later CTA on that SM
+ * reuses.  After TS_ERR_DEVICE_TIMEOUT, treat the plan's outputs and any later work on the device as
+ * unreliable: destroy the plan and reset the device (cudaDeviceReset) before relying on it again. */
 ts_status ts_plan_device_status(ts_plan plan);
 
 /* Frees the plan's device memory (synchronises the device).  NULL is accepted. */
@@ -208,12 +217,16 @@ ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n
  * It computes the same screen as ts_make_screens for a plan whose interval `screen` has length dz
  * and structure constant cn2 (no subharmonics): phi (device float32 [N][N], written) equals
  * ts_make_screens' phi[real][screen].  Its twiddles, PSD table and intermediate live in one
- * fixed-size file-scope device array (about 12 MiB) that every GPU using it holds until the process
- * exits.  Limits: N <= 1024 (larger N returns TS_ERR_WORKSPACE), screen < 64.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and sets
- * kernel attributes; make that first call before any CUDA stream capture.  All calls share the
- * array and each call overwrites it: calls that can overlap on the GPU (different streams without
- * ordering between them) race and produce wrong screens. */
+ * fixed-size file-scope device array (about 12 MiB) that every GPU on which the library's module is
+ * loaded holds until the process exits: with lazy module loading (the CUDA default) the GPUs on
+ * which a kernel of the library has run, with CUDA_MODULE_LOADING=EAGER every GPU the process opens.
+ * Limits: N <= 1024 (N = 2048 returns TS_ERR_WORKSPACE), screen < 64.
+ * Every call looks up the array's device address in the current context (cudaGetSymbolAddress: no
+ * allocation, no synchronisation), so the address is right after cudaDeviceReset and under any
+ * context the caller makes current; the first call in a context also sets kernel attributes and may
+ * load the module, so make it before any CUDA stream capture.  All calls share the array and each
+ * call overwrites it: calls that can overlap on the GPU (different streams without ordering between
+ * them) race and produce wrong screens. */
 ts_status ts_make_screen_noalloc(const ts_medium* medium, const ts_grid* grid, double dz, double cn2, uint64_t seed,
                                  uint32_t screen, uint32_t real, float* phi, void* stream);
 
@@ -263,15 +276,24 @@ ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* ph
  * (B / n_groups fields each, B divisible by n_groups).  mean, m2: device float64 [n_groups][N][N]
  * holding `count` realizations per group before the call; the chunk is merged with the pairwise
  * (Chan et al.) update, so results do not depend on how realizations are split into calls.
- * After the call each group holds count + B / n_groups realizations. */
+ * After the call each group holds count + B / n_groups realizations.
+ * beam_sums (device float64 [B][2], the per-field sums ts_propagate writes) and beam_acc (device
+ * float64 [n_groups][2]) go together or are both NULL: beam_acc[g] receives (count == 0) or adds
+ * (count > 0) the sums (sum I, sum r^2 I) of the group's fields, in increasing field order, FP64:
+ * the zeroth and second moments of the long-term spot (S23 / S24) over all realizations. */
 ts_status ts_moments_accumulate(ts_plan plan, const float* intensity, int B, int n_groups, int64_t count,
-                                double* mean, double* m2, void* stream);
+                                double* mean, double* m2, const double* beam_sums, double* beam_acc, void* stream);
 
 /* Scintillation index map SI = (m2 / count) / mean^2 (S25, population variance), its plane
- * average and the on-axis value (pixel (N/2, N/2)), for n_groups groups.  si_map: device float64
- * [n_groups][N][N] or NULL; si_mean, si_center: device float64 [n_groups] or NULL. */
+ * average and the on-axis value (pixel (N/2, N/2)), for n_groups groups; and the long-term beam
+ * radius W_LT = sqrt(2 sum_r sum_x r^2 I / sum_r sum_x I) [m] (S23 / S24 as second moments, r from
+ * pixel (N/2, N/2)) from the accumulated beam sums.  si_map: device float64 [n_groups][N][N] or
+ * NULL; si_mean, si_center, w_lt: device float64 [n_groups] or NULL; beam_acc: the device float64
+ * [n_groups][2] sums of ts_moments_accumulate (needed when w_lt is given, else may be NULL).
+ * Asynchronous on `stream` like the other calls. */
 ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2, int n_groups, int64_t count,
-                              double* si_map, double* si_mean, double* si_center, void* stream);
+                              const double* beam_acc, double* si_map, double* si_mean, double* si_center, double* w_lt,
+                              void* stream);
 
 /* Factor applied to the D2NN receiver loss and to all its gradients (default 1): e.g. 1 / max(Iref)
  * for the MAE (kind 0) or 1 / max(Iref)^2 for the squared error normalises the intensities to the

@@ -81,8 +81,8 @@ SIGNATURES = {
     "ts_evolve_screens": (_I, [_P, _U64, _U32, _U32, _D, _D, _D, _D, _P, _P, _P, _P, _P]),
     "ts_propagate": (_I, [_P, _P, _I, _P, _P, _I, _I, _U64, _U32, _P, _P, _P]),
     "ts_propagate_backward": (_I, [_P, _P, _I, _P, _P, _I, _U64, _U32, _P]),
-    "ts_moments_accumulate": (_I, [_P, _P, _I, _I, _I64, _P, _P, _P]),
-    "ts_moments_finalize": (_I, [_P, _P, _P, _I, _I64, _P, _P, _P, _P]),
+    "ts_moments_accumulate": (_I, [_P, _P, _I, _I, _I64, _P, _P, _P, _P, _P]),
+    "ts_moments_finalize": (_I, [_P, _P, _P, _I, _I64, _P, _P, _P, _P, _P, _P]),
     "ts_d2nn_forward": (_I, [_P, _P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P]),
     "ts_d2nn_backward": (_I, [_P, _I, _P, _P, _D, _P, _I, _P, _P, _P, _P, _P, _P]),
     "ts_philox4x32_10": (_I, [_P, _U32, _U32, _I, _P, _P]),
@@ -139,11 +139,13 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
-def _need(t, name: str, dtype, numel: int):
+def _need(t, name: str, dtype, numel: int, device: int | None = None):
     """Checks a buffer before its raw pointer crosses the C ABI: a CUDA tensor of `dtype` (a torch
-    dtype name, or a tuple of names any of which will do) holding at least `numel` elements.  The library receives only pointers and sizes, so
-    an undersized or mistyped buffer would be read or written out of bounds on the device; here it
-    raises on the host instead.  None passes (optional buffers)."""
+    dtype name, or a tuple of names any of which will do) holding at least `numel` elements, on GPU
+    `device` when one is given.  The library receives only pointers and sizes, so an undersized or
+    mistyped buffer, or one that lives on another GPU than the kernels run on, would be read or
+    written out of bounds on the device; here it raises on the host instead.  None passes (optional
+    buffers)."""
     if t is None:
         return
     import torch
@@ -154,15 +156,36 @@ def _need(t, name: str, dtype, numel: int):
         raise TypeError(f"{name} must be torch.{' or torch.'.join(names)}, got {t.dtype}")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, but the call runs on cuda:{device}")
     if t.numel() < numel:
         raise ValueError(f"{name} holds {t.numel()} elements, the call needs {numel}")
 
 
-def _stream(stream) -> int | None:
+def _stream(stream, device: int | None = None) -> int | None:
+    """The raw cudaStream_t of `stream`, or of `device`'s current stream when stream is None."""
     if stream is None:
         import torch
-        return torch.cuda.current_stream().cuda_stream
+        return torch.cuda.current_stream(device).cuda_stream
     return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _on(device: int):
+    """Context that makes `device` the current CUDA device for the duration of one library call (the
+    library enqueues its work on the current device)."""
+    import torch
+    return torch.cuda.device(device)
+
+
+def _device_of(*tensors) -> int:
+    """The GPU index shared by the given tensors (None entries skipped); raises if they differ."""
+    devs = {t.device.index for t in tensors if t is not None and getattr(t, "is_cuda", False)}
+    if len(devs) > 1:
+        raise ValueError(f"buffers of one call live on different GPUs: {sorted(devs)}")
+    if not devs:
+        import torch
+        return torch.cuda.current_device()
+    return devs.pop()
 
 
 def max_step(lam, N, dx, n0=1.0) -> float:
@@ -173,10 +196,12 @@ def max_step(lam, N, dx, n0=1.0) -> float:
 def adam_step(param, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     """One Adam step on device float32 tensors (see ts_adam_step); t >= 1."""
     n = int(param.numel())
+    dev = _device_of(param)
     for t_, nm in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
-        _need(t_, nm, "float32", n)
-    _check(load().ts_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, float(lr), float(beta1),
-                               float(beta2), float(eps), int(t), _stream(stream)), "ts_adam_step")
+        _need(t_, nm, "float32", n, dev)
+    with _on(dev):
+        _check(load().ts_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, float(lr), float(beta1),
+                                   float(beta2), float(eps), int(t), _stream(stream, dev)), "ts_adam_step")
 
 
 def _host_f64(x):
@@ -225,10 +250,12 @@ def place_screens(prof_z, prof_cn2, lam, N, dx, L, rytov_limit, init_bounds=None
 def philox4x32_10(ctr, key0, key1, out, stream=None):
     """Philox4x32-10 words of n counters (ctr, out: device uint32 tensors of 4n words)."""
     n = ctr.numel() // 4
-    _need(ctr, "ctr", ("int32", "uint32"), 4 * n)  # 32-bit words
-    _need(out, "out", ("int32", "uint32"), 4 * n)
-    _check(load().ts_philox4x32_10(_ptr(ctr), int(key0), int(key1), n, _ptr(out), _stream(stream)),
-           "ts_philox4x32_10")
+    dev = _device_of(ctr)
+    _need(ctr, "ctr", ("int32", "uint32"), 4 * n, dev)  # 32-bit words
+    _need(out, "out", ("int32", "uint32"), 4 * n, dev)
+    with _on(dev):
+        _check(load().ts_philox4x32_10(_ptr(ctr), int(key0), int(key1), n, _ptr(out), _stream(stream, dev)),
+               "ts_philox4x32_10")
 
 
 def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0, l0=0.0, L0=0.0, stream=None):
@@ -236,10 +263,12 @@ def make_screen_noalloc(phi, lam, N, dx, dz, cn2, seed, screen=0, real=0, n0=1.0
     ts_make_screen_noalloc in include/turbscreen.h."""
     L0v = float(L0) if (L0 is not None and math.isfinite(L0)) else 0.0
     med = Medium(float(lam), float(n0), float(l0), L0v)
-    _need(phi, "phi", "float32", int(N) * int(N))
-    _check(load().ts_make_screen_noalloc(C.byref(med), C.byref(Grid(int(N), float(dx))), float(dz), float(cn2),
-                                         int(seed), int(screen), int(real), _ptr(phi), _stream(stream)),
-           "ts_make_screen_noalloc")
+    dev = _device_of(phi)
+    _need(phi, "phi", "float32", int(N) * int(N), dev)
+    with _on(dev):  # the scratch array's address is looked up on the current device
+        _check(load().ts_make_screen_noalloc(C.byref(med), C.byref(Grid(int(N), float(dx))), float(dz), float(cn2),
+                                             int(seed), int(screen), int(real), _ptr(phi), _stream(stream, dev)),
+               "ts_make_screen_noalloc")
 
 
 def tc_dft32(x, X, sign=-1, layout=0, err=None, timeout_s=1.0, stream=None):
@@ -248,12 +277,14 @@ def tc_dft32(x, X, sign=-1, layout=0, err=None, timeout_s=1.0, stream=None):
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device=x.device)
     nvec = x.numel() // 32
-    _need(x, "x", "complex64", 32 * nvec)
-    _need(X, "X", "complex64", 32 * nvec)
-    _need(err, "err", "int32", 1)
-    _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), int(layout), float(timeout_s), _ptr(err),
-                              _stream(stream)),
-           "ts_tc_dft32")
+    dev = _device_of(x)
+    _need(x, "x", "complex64", 32 * nvec, dev)
+    _need(X, "X", "complex64", 32 * nvec, dev)
+    _need(err, "err", "int32", 1, dev)
+    with _on(dev):
+        _check(load().ts_tc_dft32(_ptr(x), _ptr(X), nvec, int(sign), int(layout), float(timeout_s), _ptr(err),
+                                  _stream(stream, dev)),
+               "ts_tc_dft32")
     return err
 
 
@@ -293,6 +324,8 @@ class Plan:
             _check(lib.ts_plan_create_psd(C.byref(h), C.byref(med), C.byref(grid), C.byref(path), int(sh_levels),
                                           int(max_batch), int(flags), a, A), "ts_plan_create_psd")
         self._h = h
+        import torch
+        self.device = torch.cuda.current_device()  # the plan's tables and workspace live here
 
     @property
     def handle(self):
@@ -338,11 +371,16 @@ class Plan:
         """Waits for the device and raises TsError (TS_ERR_DEVICE_TIMEOUT) if a bounded device wait of
         the plan's passes (tensor-core MMAs, or the TMA copies of the prefetching variants) ran out of its
         budget since the last call."""
-        _check(load().ts_plan_device_status(self._h), "ts_plan_device_status")
+        with _on(self.device):
+            _check(load().ts_plan_device_status(self._h), "ts_plan_device_status")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            load().ts_plan_destroy(self._h)
+            try:
+                with _on(self.device):
+                    load().ts_plan_destroy(self._h)
+            except Exception:  # interpreter shutdown: torch may already be gone
+                load().ts_plan_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):
@@ -354,7 +392,8 @@ class Plan:
     def timing(self, enable: bool, capacity: int = 0):
         """Record CUDA events around each launch (kinds: 0 column pass, 1 row pass, 2 screens, 3 fused
         propagation)."""
-        _check(load().ts_plan_timing(self._h, 1 if enable else 0, int(capacity)), "ts_plan_timing")
+        with _on(self.device):
+            _check(load().ts_plan_timing(self._h, 1 if enable else 0, int(capacity)), "ts_plan_timing")
 
     def timing_read(self, kind: int):
         """(number of timed launches, summed device milliseconds) for one kernel kind."""
@@ -364,96 +403,117 @@ class Plan:
 
     def set_sources(self, w0):
         w = (C.c_double * len(w0))(*[float(x) for x in w0])
-        _check(load().ts_plan_set_sources(self._h, len(w0), w), "ts_plan_set_sources")
+        with _on(self.device):
+            _check(load().ts_plan_set_sources(self._h, len(w0), w), "ts_plan_set_sources")
 
     def _n2(self) -> int:
         return self.N * self.N
 
     def make_sources(self, field, B, stream=None):
-        _need(field, "field", "complex64", int(B) * self._n2())
-        _check(load().ts_make_sources(self._h, _ptr(field), int(B), _stream(stream)), "ts_make_sources")
+        _need(field, "field", "complex64", int(B) * self._n2(), self.device)
+        with _on(self.device):
+            _check(load().ts_make_sources(self._h, _ptr(field), int(B), _stream(stream, self.device)), "ts_make_sources")
 
     def make_screens(self, phi, seed, real_base=0, n_real=1, phasor=None, stream=None):
         n = int(n_real) * self.S * self._n2()
-        _need(phi, "phi", "float32", n)
-        _need(phasor, "phasor", "complex64", n)
-        _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _ptr(phasor),
-                                      _stream(stream)), "ts_make_screens")
+        _need(phi, "phi", "float32", n, self.device)
+        _need(phasor, "phasor", "complex64", n, self.device)
+        with _on(self.device):
+            _check(load().ts_make_screens(self._h, int(seed), int(real_base), int(n_real), _ptr(phi), _ptr(phasor),
+                                          _stream(stream, self.device)), "ts_make_screens")
 
     def evolve_screens(self, spec, phi, seed, t, alpha, real=0, vx=0.0, vy=0.0, T=0.0, sh_state=None, phasor=None,
                        stream=None):
         n = self.S * self._n2()
-        _need(spec, "spec", "complex64", n)
-        _need(phi, "phi", "float32", n)
-        _need(phasor, "phasor", "complex64", n)
-        _need(sh_state, "sh_state", "complex128", self.S * 27)
-        _check(load().ts_evolve_screens(self._h, int(seed), int(real), int(t), float(alpha), float(vx), float(vy),
-                                        float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _ptr(phasor),
-                                        _stream(stream)), "ts_evolve_screens")
+        _need(spec, "spec", "complex64", n, self.device)
+        _need(phi, "phi", "float32", n, self.device)
+        _need(phasor, "phasor", "complex64", n, self.device)
+        _need(sh_state, "sh_state", "complex128", self.S * 27, self.device)
+        with _on(self.device):
+            _check(load().ts_evolve_screens(self._h, int(seed), int(real), int(t), float(alpha), float(vx), float(vy),
+                                            float(T), _ptr(spec), _ptr(sh_state), _ptr(phi), _ptr(phasor),
+                                            _stream(stream, self.device)), "ts_evolve_screens")
 
     def propagate(self, field, B, phi=None, phi_group=1, flags=0, seed=0, real_base=0, intensity=None,
                   beam_sums=None, phasor=None, stream=None):
         self._need_path(field, "field", B, phi, phasor, phi_group)
-        _need(intensity, "intensity", "float32", int(B) * self._n2())
-        _need(beam_sums, "beam_sums", "float64", 2 * int(B))
-        _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), _ptr(phasor), int(phi_group), int(flags),
-                                   int(seed), int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream)),
-               "ts_propagate")
+        _need(intensity, "intensity", "float32", int(B) * self._n2(), self.device)
+        _need(beam_sums, "beam_sums", "float64", 2 * int(B), self.device)
+        with _on(self.device):
+            _check(load().ts_propagate(self._h, _ptr(field), int(B), _ptr(phi), _ptr(phasor), int(phi_group), int(flags),
+                                       int(seed), int(real_base), _ptr(intensity), _ptr(beam_sums), _stream(stream, self.device)),
+                   "ts_propagate")
 
     def _need_path(self, field, name, B, phi, phasor, phi_group):
         """The field [B][N][N] and the screen sets [ceil(B / phi_group)][S][N][N] of a propagation."""
         B, g = int(B), max(1, int(phi_group))
-        _need(field, name, "complex64", B * self._n2())
+        _need(field, name, "complex64", B * self._n2(), self.device)
         n = -(-B // g) * self.S * self._n2()
-        _need(phi, "phi", "float32", n)
-        _need(phasor, "phasor", "complex64", n)
+        _need(phi, "phi", "float32", n, self.device)
+        _need(phasor, "phasor", "complex64", n, self.device)
 
     def propagate_backward(self, grad, B, phi=None, phi_group=1, seed=0, real_base=0, phasor=None, stream=None):
         self._need_path(grad, "grad", B, phi, phasor, phi_group)
-        _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), _ptr(phasor), int(phi_group),
-                                            int(seed), int(real_base), _stream(stream)), "ts_propagate_backward")
+        with _on(self.device):
+            _check(load().ts_propagate_backward(self._h, _ptr(grad), int(B), _ptr(phi), _ptr(phasor), int(phi_group),
+                                                int(seed), int(real_base), _stream(stream, self.device)), "ts_propagate_backward")
 
-    def moments_accumulate(self, intensity, B, n_groups, count, mean, m2, stream=None):
-        _need(intensity, "intensity", "float32", int(B) * self._n2())
-        _need(mean, "mean", "float64", int(n_groups) * self._n2())
-        _need(m2, "m2", "float64", int(n_groups) * self._n2())
-        _check(load().ts_moments_accumulate(self._h, _ptr(intensity), int(B), int(n_groups), int(count), _ptr(mean),
-                                            _ptr(m2), _stream(stream)), "ts_moments_accumulate")
+    def moments_accumulate(self, intensity, B, n_groups, count, mean, m2, beam_sums=None, beam_acc=None,
+                           stream=None):
+        """FP64 Welford merge of B intensities into the n_groups running (mean, m2); with beam_sums (the
+        [B][2] sums of propagate) also the groups' running beam sums beam_acc [n_groups][2]."""
+        _need(intensity, "intensity", "float32", int(B) * self._n2(), self.device)
+        _need(mean, "mean", "float64", int(n_groups) * self._n2(), self.device)
+        _need(m2, "m2", "float64", int(n_groups) * self._n2(), self.device)
+        _need(beam_sums, "beam_sums", "float64", 2 * int(B), self.device)
+        _need(beam_acc, "beam_acc", "float64", 2 * int(n_groups), self.device)
+        with _on(self.device):
+            _check(load().ts_moments_accumulate(self._h, _ptr(intensity), int(B), int(n_groups), int(count), _ptr(mean),
+                                                _ptr(m2), _ptr(beam_sums), _ptr(beam_acc),
+                                                _stream(stream, self.device)), "ts_moments_accumulate")
 
-    def moments_finalize(self, mean, m2, n_groups, count, si_map=None, si_mean=None, si_center=None, stream=None):
+    def moments_finalize(self, mean, m2, n_groups, count, si_map=None, si_mean=None, si_center=None, beam_acc=None,
+                         w_lt=None, stream=None):
+        """SI map, plane-mean SI and on-axis SI per group; with beam_acc, the long-term radius w_lt [m]."""
         n = int(n_groups) * self._n2()
-        _need(mean, "mean", "float64", n)
-        _need(m2, "m2", "float64", n)
-        _need(si_map, "si_map", "float64", n)
-        _need(si_mean, "si_mean", "float64", int(n_groups))
-        _need(si_center, "si_center", "float64", int(n_groups))
-        _check(load().ts_moments_finalize(self._h, _ptr(mean), _ptr(m2), int(n_groups), int(count), _ptr(si_map),
-                                          _ptr(si_mean), _ptr(si_center), _stream(stream)), "ts_moments_finalize")
+        _need(mean, "mean", "float64", n, self.device)
+        _need(m2, "m2", "float64", n, self.device)
+        _need(si_map, "si_map", "float64", n, self.device)
+        _need(si_mean, "si_mean", "float64", int(n_groups), self.device)
+        _need(si_center, "si_center", "float64", int(n_groups), self.device)
+        _need(beam_acc, "beam_acc", "float64", 2 * int(n_groups), self.device)
+        _need(w_lt, "w_lt", "float64", int(n_groups), self.device)
+        with _on(self.device):
+            _check(load().ts_moments_finalize(self._h, _ptr(mean), _ptr(m2), int(n_groups), int(count), _ptr(beam_acc),
+                                              _ptr(si_map), _ptr(si_mean), _ptr(si_center), _ptr(w_lt),
+                                              _stream(stream, self.device)), "ts_moments_finalize")
 
     def _need_d2nn(self, B, th1, th2, Iref, ws, intensity):
         n2, B = self._n2(), int(B)
-        _need(th1, "th1", "float32", n2)
-        _need(th2, "th2", "float32", n2)
-        _need(Iref, "Iref", "float32", n2)
-        _need(ws, "ws", "complex64", 3 * B * n2)
-        _need(intensity, "intensity", "float32", B * n2)
+        _need(th1, "th1", "float32", n2, self.device)
+        _need(th2, "th2", "float32", n2, self.device)
+        _need(Iref, "Iref", "float32", n2, self.device)
+        _need(ws, "ws", "complex64", 3 * B * n2, self.device)
+        _need(intensity, "intensity", "float32", B * n2, self.device)
 
     def d2nn_forward(self, U, B, th1, th2, aperture, Iref, kind, ws, intensity, loss, stream=None):
-        _need(U, "U", "complex64", int(B) * self._n2())
+        _need(U, "U", "complex64", int(B) * self._n2(), self.device)
         self._need_d2nn(B, th1, th2, Iref, ws, intensity)
-        _need(loss, "loss", "float64", 1)
-        _check(load().ts_d2nn_forward(self._h, _ptr(U), int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref),
-                                      int(kind), _ptr(ws), _ptr(intensity), _ptr(loss), _stream(stream)),
-               "ts_d2nn_forward")
+        _need(loss, "loss", "float64", 1, self.device)
+        with _on(self.device):
+            _check(load().ts_d2nn_forward(self._h, _ptr(U), int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref),
+                                          int(kind), _ptr(ws), _ptr(intensity), _ptr(loss), _stream(stream, self.device)),
+                   "ts_d2nn_forward")
 
     def d2nn_backward(self, B, th1, th2, aperture, Iref, kind, ws, intensity, g_th1, g_th2, gU, stream=None):
         self._need_d2nn(B, th1, th2, Iref, ws, intensity)
-        _need(g_th1, "g_th1", "float32", self._n2())
-        _need(g_th2, "g_th2", "float32", self._n2())
-        _need(gU, "gU", "complex64", int(B) * self._n2())
-        _check(load().ts_d2nn_backward(self._h, int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref), int(kind),
-                                       _ptr(ws), _ptr(intensity), _ptr(g_th1), _ptr(g_th2), _ptr(gU),
-                                       _stream(stream)), "ts_d2nn_backward")
+        _need(g_th1, "g_th1", "float32", self._n2(), self.device)
+        _need(g_th2, "g_th2", "float32", self._n2(), self.device)
+        _need(gU, "gU", "complex64", int(B) * self._n2(), self.device)
+        with _on(self.device):
+            _check(load().ts_d2nn_backward(self._h, int(B), _ptr(th1), _ptr(th2), float(aperture), _ptr(Iref), int(kind),
+                                           _ptr(ws), _ptr(intensity), _ptr(g_th1), _ptr(g_th2), _ptr(gU),
+                                           _stream(stream, self.device)), "ts_d2nn_backward")
 
 
 class Batch:
@@ -462,10 +522,13 @@ class Batch:
     def __init__(self, instances, timeout_s=5.0, flags=0):
         """instances: list of dicts with keys plan, field, phasor (or None), seed, real, source."""
         arr = (BatchInstance * len(instances))()
+        self.device = instances[0]["plan"].device if instances else None
         for i, d in enumerate(instances):
             pl = d["plan"]
-            _need(d["field"], f"instances[{i}].field", "complex64", pl.N * pl.N)
-            _need(d.get("phasor"), f"instances[{i}].phasor", "complex64", pl.S * pl.N * pl.N)
+            if pl.device != self.device:
+                raise ValueError(f"instances[{i}].plan lives on cuda:{pl.device}, instance 0 on cuda:{self.device}")
+            _need(d["field"], f"instances[{i}].field", "complex64", pl.N * pl.N, self.device)
+            _need(d.get("phasor"), f"instances[{i}].phasor", "complex64", pl.S * pl.N * pl.N, self.device)
             arr[i].plan = pl.handle.value
             arr[i].field = _ptr(d["field"])
             arr[i].phasor = _ptr(d.get("phasor"))
@@ -474,16 +537,19 @@ class Batch:
             arr[i].source = 1 if d.get("source") else 0
         self._keep = [d["plan"] for d in instances]
         h = C.c_void_p()
-        _check(load().ts_batch_create(C.byref(h), arr, len(instances), float(timeout_s), int(flags)),
-               "ts_batch_create")
+        with _on(self.device):
+            _check(load().ts_batch_create(C.byref(h), arr, len(instances), float(timeout_s), int(flags)),
+                   "ts_batch_create")
         self._h = h
 
     def run(self, stream=None):
-        _check(load().ts_batch_run(self._h, _stream(stream)), "ts_batch_run")
+        with _on(self.device):
+            _check(load().ts_batch_run(self._h, _stream(stream, self.device)), "ts_batch_run")
 
     def status(self, stream=None) -> int:
         """0, or the TS_ERR_* code the device reported (does not raise)."""
-        return load().ts_batch_status(self._h, _stream(stream))
+        with _on(self.device):
+            return load().ts_batch_status(self._h, _stream(stream, self.device))
 
     def info(self):
         n, g, b = C.c_int(), C.c_int(), C.c_size_t()

@@ -37,6 +37,20 @@ ts_status fail(ts_status st, const std::string& msg)
     return st;
 }
 
+// Every call that launches work or touches the plan's memory runs on the device the plan was created
+// on: the kernels receive raw pointers into that device's memory, so a call made while another device
+// is current would hand them addresses they cannot reach.
+ts_status check_device(const Plan& p, const char* where)
+{
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, where);
+    if (dev != p.device)
+        return fail(TS_ERR_INVALID_ARG, std::string(where) + ": the plan lives on device " + std::to_string(p.device) +
+                                            " but device " + std::to_string(dev) + " is current");
+    return TS_OK;
+}
+
 bool supported_N(int N) { return N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048; }
 
 double wavenumber(const ts_medium* m) { return 2.0 * M_PI * m->n0 / m->lambda; }
@@ -856,6 +870,7 @@ ts_status ts_plan_device_status(ts_plan plan)
 {
     if (!plan) return fail(TS_ERR_INVALID_ARG, "ts_plan_device_status: null plan");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_plan_device_status"); sd != TS_OK) return sd;
     if (!p->d_err) return TS_OK;
     int code = 0;
     cudaError_t e = cudaDeviceSynchronize();
@@ -870,6 +885,7 @@ ts_status ts_plan_set_sources(ts_plan plan, int n, const double* w0)
 {
     if (!plan || !w0 || n < 1 || n > kMaxSources) return fail(TS_ERR_INVALID_ARG, "need a plan and 1..64 source waists");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_plan_set_sources"); sd != TS_OK) return sd;
     for (int i = 0; i < n; ++i) p->src_coef[i] = w0[i] > 0.0 ? (float)(p->dx * p->dx / (w0[i] * w0[i])) : -1.0f;
     p->n_src = n;
     if (p->src_fx) {
@@ -905,6 +921,7 @@ ts_status ts_make_sources(ts_plan plan, void* field, int B, void* stream)
 {
     if (!plan || !field || B < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_sources: need plan, field and B >= 1");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_make_sources"); sd != TS_OK) return sd;
     if (p->n_src < 1) return fail(TS_ERR_INVALID_ARG, "ts_make_sources: no source table set");
     RowArgs ra{};
     ra.field = reinterpret_cast<float2*>(field);
@@ -919,6 +936,7 @@ ts_status ts_make_screens(ts_plan plan, uint64_t seed, uint32_t real_base, int n
     if (!plan || (!phi && !phasor) || n_real < 1)
         return fail(TS_ERR_INVALID_ARG, "ts_make_screens: need plan, phi or phasor, and n_real >= 1");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_make_screens"); sd != TS_OK) return sd;
     ScreenArgs a{};
     a.seed = seed;
     a.s_begin = 0;
@@ -938,6 +956,7 @@ ts_status ts_evolve_screens(ts_plan plan, uint64_t seed, uint32_t real, uint32_t
     if (!plan || !spec || (!phi && !phasor))
         return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: need plan, spec, and phi or phasor");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_evolve_screens"); sd != TS_OK) return sd;
     if (p->sh_levels && !sh_state) return fail(TS_ERR_INVALID_ARG, "ts_evolve_screens: plan has subharmonics, sh_state needed");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(TS_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
     if (t > 0xFFFFFFu) return fail(TS_ERR_INVALID_ARG, "t must be below 2^24");
@@ -974,6 +993,7 @@ ts_status ts_propagate(ts_plan plan, void* field, int B, const float* phi, const
 {
     if (!plan || !field) return fail(TS_ERR_INVALID_ARG, "ts_propagate: need plan and field");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_propagate"); sd != TS_OK) return sd;
     if (B < 1 || phi_group < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate: B and phi_group must be >= 1");
     if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_propagate: B exceeds the plan's max_batch");
     if ((flags & TS_PROP_SOURCE) && p->n_src < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate: no source table set");
@@ -996,6 +1016,7 @@ ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* ph
 {
     if (!plan || !grad) return fail(TS_ERR_INVALID_ARG, "ts_propagate_backward: need plan and grad");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_propagate_backward"); sd != TS_OK) return sd;
     if (B < 1 || phi_group < 1) return fail(TS_ERR_INVALID_ARG, "ts_propagate_backward: B and phi_group must be >= 1");
     if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_propagate_backward: B exceeds the plan's max_batch");
     cudaStream_t st = as_stream(stream);
@@ -1055,23 +1076,39 @@ ts_status ts_propagate_backward(ts_plan plan, void* grad, int B, const float* ph
 }
 
 ts_status ts_moments_accumulate(ts_plan plan, const float* intensity, int B, int n_groups, int64_t count, double* mean,
-                                double* m2, void* stream)
+                                double* m2, const double* beam_sums, double* beam_acc, void* stream)
 {
     if (!plan || !intensity || !mean || !m2) return fail(TS_ERR_INVALID_ARG, "ts_moments_accumulate: null pointer");
+    if ((beam_sums == nullptr) != (beam_acc == nullptr))
+        return fail(TS_ERR_INVALID_ARG, "ts_moments_accumulate: beam_sums and beam_acc go together");
     if (n_groups < 1 || B < n_groups || B % n_groups != 0 || count < 0)
         return fail(TS_ERR_INVALID_ARG, "ts_moments_accumulate: B must be a positive multiple of n_groups");
     Plan* p = reinterpret_cast<Plan*>(plan);
-    return cuda_check(launch_moments(*p, intensity, B, n_groups, count, mean, m2, as_stream(stream)),
-                      "ts_moments_accumulate");
+    if (ts_status sd = check_device(*p, "ts_moments_accumulate"); sd != TS_OK) return sd;
+    cudaStream_t st = as_stream(stream);
+    if (beam_sums) {
+        ts_status sb = cuda_check(launch_beam_acc(beam_sums, B, n_groups, count == 0, beam_acc, st),
+                                  "ts_moments_accumulate beam sums");
+        if (sb != TS_OK) return sb;
+    }
+    return cuda_check(launch_moments(*p, intensity, B, n_groups, count, mean, m2, st), "ts_moments_accumulate");
 }
 
 ts_status ts_moments_finalize(ts_plan plan, const double* mean, const double* m2, int n_groups, int64_t count,
-                              double* si_map, double* si_mean, double* si_center, void* stream)
+                              const double* beam_acc, double* si_map, double* si_mean, double* si_center, double* w_lt,
+                              void* stream)
 {
     if (!plan || !mean || !m2 || n_groups < 1 || count < 1)
         return fail(TS_ERR_INVALID_ARG, "ts_moments_finalize: need moments with count >= 1");
+    if (w_lt && !beam_acc) return fail(TS_ERR_INVALID_ARG, "ts_moments_finalize: w_lt needs beam_acc");
     Plan* p = reinterpret_cast<Plan*>(plan);
-    return cuda_check(launch_moments_finalize(*p, mean, m2, n_groups, count, si_map, si_mean, si_center, as_stream(stream)),
+    if (ts_status sd = check_device(*p, "ts_moments_finalize"); sd != TS_OK) return sd;
+    cudaStream_t st = as_stream(stream);
+    if (w_lt) {
+        ts_status sw = cuda_check(launch_w_lt(beam_acc, n_groups, w_lt, st), "ts_moments_finalize w_lt");
+        if (sw != TS_OK) return sw;
+    }
+    return cuda_check(launch_moments_finalize(*p, mean, m2, n_groups, count, si_map, si_mean, si_center, st),
                       "ts_moments_finalize");
 }
 
@@ -1079,6 +1116,7 @@ ts_status ts_plan_timing(ts_plan plan, int enable, int capacity)
 {
     if (!plan || capacity < 0) return fail(TS_ERR_INVALID_ARG, "ts_plan_timing: need a plan and capacity >= 0");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_plan_timing"); sd != TS_OK) return sd;
     destroy_events(p);
     p->timing = enable != 0;
     if (!p->timing) return TS_OK;
@@ -1126,6 +1164,7 @@ ts_status ts_d2nn_forward(ts_plan plan, const void* U, int B, const float* th1, 
     if (!plan || !U || !th1 || !th2 || !Iref || !ws || !intensity || !loss)
         return fail(TS_ERR_INVALID_ARG, "ts_d2nn_forward: null pointer");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_d2nn_forward"); sd != TS_OK) return sd;
     if (B < 1 || (kind != 0 && kind != 1) || !(aperture > 0.0))
         return fail(TS_ERR_INVALID_ARG, "ts_d2nn_forward: need B >= 1, kind 0/1 and aperture > 0");
     if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_d2nn_forward: B exceeds the plan's max_batch");
@@ -1150,6 +1189,7 @@ ts_status ts_d2nn_backward(ts_plan plan, int B, const float* th1, const float* t
     if (!plan || !th1 || !th2 || !Iref || !ws || !intensity || !g_th1 || !g_th2 || !gU)
         return fail(TS_ERR_INVALID_ARG, "ts_d2nn_backward: null pointer");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    if (ts_status sd = check_device(*p, "ts_d2nn_backward"); sd != TS_OK) return sd;
     if (B < 1 || (kind != 0 && kind != 1) || !(aperture > 0.0))
         return fail(TS_ERR_INVALID_ARG, "ts_d2nn_backward: need B >= 1, kind 0/1 and aperture > 0");
     if (B > p->max_batch) return fail(TS_ERR_WORKSPACE, "ts_d2nn_backward: B exceeds the plan's max_batch");

@@ -386,6 +386,10 @@ ts_status ts_batch_run(ts_batch batch, void* stream)
 {
     if (!batch) return bfail(TS_ERR_INVALID_ARG, "ts_batch_run: null batch");
     Batch* b = reinterpret_cast<Batch*>(batch);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return bfail(TS_ERR_INVALID_ARG, "ts_batch_run: the batch lives on device " + std::to_string(b->device) +
+                                             ", which must be current");
     return cuda_check(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)), "ts_batch_run");
 }
 

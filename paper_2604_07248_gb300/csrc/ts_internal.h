@@ -187,7 +187,11 @@ cudaError_t prepare_d2nn_kernels(int N);
 // moments
 cudaError_t launch_moments(const Plan& p, const float* I, int B, int G, int64_t count, double* mean, double* m2,
                            cudaStream_t st);
+// per-group running beam sums: acc[g] (+)= sum over fields b = g mod G of (sum I, sum r^2 I)
+cudaError_t launch_beam_acc(const double* beam_sums, int B, int G, bool first, double* acc, cudaStream_t st);
 cudaError_t launch_moments_finalize(const Plan& p, const double* mean, const double* m2, int G, int64_t count,
                                     double* si_map, double* si_mean, double* si_center, cudaStream_t st);
+// w_lt[g] = sqrt(2 acc[g][1] / acc[g][0])
+cudaError_t launch_w_lt(const double* acc, int G, double* w_lt, cudaStream_t st);
 
 }  // namespace ts

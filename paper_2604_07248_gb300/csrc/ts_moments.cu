@@ -1,4 +1,5 @@
-// ts_moments.cu -- per-pixel intensity moments across realizations in FP64 (S25, Welford).
+// ts_moments.cu -- per-pixel intensity moments across realizations in FP64 (S25, Welford), and the
+// long-term beam radius W_LT from the accumulated beam sums (S23 / S24).
 //
 // Each call merges one chunk (the fields of a group) into running (count, mean, M2) with the
 // pairwise update of Chan, Golub and LeVeque: the chunk's own mean and M2 are formed in FP64 by two
@@ -63,7 +64,40 @@ __global__ void __launch_bounds__(256) si_kernel(const double* __restrict__ mean
     if (threadIdx.x == 0 && si_mean) si_mean[g] = red[0] / (double)npix;
 }
 
+// Beam sums of one chunk, per group, in increasing field order (FP64): the long-term spot's zeroth
+// and second moments accumulated over realizations (S23 / S24).
+__global__ void beam_acc_kernel(const double* __restrict__ sums, int B, int G, bool first, double* __restrict__ acc)
+{
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int b = g; b < B; b += G) {
+            s0 += sums[2 * b];
+            s1 += sums[2 * b + 1];
+        }
+        acc[2 * g] = first ? s0 : acc[2 * g] + s0;
+        acc[2 * g + 1] = first ? s1 : acc[2 * g + 1] + s1;
+    }
+}
+
+// second-moment radius of the long-term spot, W_LT^2 = 2 sum r^2 I / sum I (S23 / S24 reading)
+__global__ void w_lt_kernel(const double* __restrict__ acc, int G, double* __restrict__ w)
+{
+    for (int g = threadIdx.x; g < G; g += blockDim.x) w[g] = sqrt(2.0 * acc[2 * g + 1] / acc[2 * g]);
+}
+
 }  // namespace
+
+cudaError_t launch_beam_acc(const double* beam_sums, int B, int G, bool first, double* acc, cudaStream_t st)
+{
+    beam_acc_kernel<<<1, 128, 0, st>>>(beam_sums, B, G, first, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_w_lt(const double* acc, int G, double* w_lt, cudaStream_t st)
+{
+    w_lt_kernel<<<1, 128, 0, st>>>(acc, G, w_lt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_moments(const Plan& p, const float* I, int B, int G, int64_t count, double* mean, double* m2,
                            cudaStream_t st)

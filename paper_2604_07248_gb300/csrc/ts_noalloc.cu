@@ -8,12 +8,19 @@
 // shape table and column-transformed intermediate in one file-scope device array of fixed size,
 // so it allocates nothing.  It launches the same screen-synthesis kernels as ts_make_screens.
 //
-// The array lives in this file's module: every GPU on which the library uses it holds it
-// (kNoAllocBytes, about 12 MiB) until the process exits.  Host code cannot use the array's name
-// as a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it.
+// The array lives in this file's module: every GPU on which the library's module is loaded holds it
+// (kNoAllocBytes, about 12 MiB) until the process exits.  With lazy module loading (the CUDA default)
+// that is every GPU on which a kernel of the library has run; with CUDA_MODULE_LOADING=EAGER it is
+// every GPU the process opens.  Host code cannot use the array's name as a device address, so every
+// call looks the address up in the current context with cudaGetSymbolAddress (a host-side query: no
+// allocation, no synchronisation), which stays correct after cudaDeviceReset or under a context the
+// caller made current through the driver API.  The first call in a context also sets the synthesis
+// kernels' shared-memory limits; contexts are told apart by their process-unique id.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
+#include <utility>
 #include <string>
 
 #include "ts_internal.h"
@@ -33,35 +40,58 @@ constexpr size_t kNoAllocBytes = kOffAmp + round_up(sizeof(float) * kMaxScreens)
 
 static __device__ __align__(256) unsigned char ts_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_scratch[kMaxDevices] = {};
+constexpr int kMaxContexts = 64;
+unsigned long long g_ready[kMaxContexts] = {};  // ids of the contexts whose kernel limits are set
+int g_n_ready = 0;
 
 __global__ void store_amplitude(float* amp, int s, float v) { amp[s] = v; }
 
-// Per-device set-up, done by the first call on each device: the device address of the array and
-// the shared-memory limits of the synthesis kernels.
-ts_status scratch_for_current_device(unsigned char** out)
+// The process-unique id of the current context (cuCtxGetCurrent + cuCtxGetId, reached through the
+// runtime's driver entry-point query), or 0 when it cannot be read.
+unsigned long long current_context_id()
 {
-    int dev = 0;
-    ts_status st = cuda_check(cudaGetDevice(&dev), "ts_make_screen_noalloc: cudaGetDevice");
+    using GetCurrentFn = CUresult (*)(CUcontext*);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+    static const auto fns = []() {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa = cudaDriverEntryPointSymbolNotFound, qb = qa;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess)
+            a = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qb != cudaDriverEntryPointSuccess)
+            b = nullptr;
+        return std::make_pair(reinterpret_cast<GetCurrentFn>(a), reinterpret_cast<GetIdFn>(b));
+    }();
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!fns.first || !fns.second || fns.first(&ctx) != CUDA_SUCCESS || !ctx || fns.second(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// The device address of the array in the current context, and (first call in a context) the
+// shared-memory limits of the synthesis kernels.
+ts_status scratch_for_current_context(unsigned char** out)
+{
+    void* ptr = nullptr;  // also brings up the current device's primary context if none is current
+    ts_status st =
+        cuda_check(cudaGetSymbolAddress(&ptr, ts_noalloc_scratch), "ts_make_screen_noalloc: cudaGetSymbolAddress");
     if (st != TS_OK) return st;
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("ts_make_screen_noalloc: device ordinal above 63");
-        return TS_ERR_UNSUPPORTED;
-    }
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch[dev] == nullptr) {
-        void* ptr = nullptr;
-        st = cuda_check(cudaGetSymbolAddress(&ptr, ts_noalloc_scratch), "ts_make_screen_noalloc: cudaGetSymbolAddress");
-        if (st != TS_OK) return st;
+    bool ready = false;
+    for (int i = 0; i < g_n_ready && id != 0; ++i) ready = ready || g_ready[i] == id;
+    if (!ready) {
         for (int n = 128; n <= kNoAllocMaxN; n *= 2) {
             st = cuda_check(prepare_screen_kernels(n), "ts_make_screen_noalloc: kernel attributes");
             if (st != TS_OK) return st;
         }
-        g_scratch[dev] = static_cast<unsigned char*>(ptr);
+        if (id != 0 && g_n_ready < kMaxContexts) g_ready[g_n_ready++] = id;
     }
-    *out = g_scratch[dev];
+    *out = static_cast<unsigned char*>(ptr);
     return TS_OK;
 }
 
@@ -79,7 +109,7 @@ extern "C" ts_status ts_make_screen_noalloc(const ts_medium* medium, const ts_gr
     }
     const int N = grid->N;
     if (N != 128 && N != 256 && N != 512 && N != 1024 && N != 2048) {
-        set_error("ts_make_screen_noalloc: N must be one of 128, 256, 512, 1024");
+        set_error("ts_make_screen_noalloc: N must be one of 128, 256, 512, 1024, 2048");
         return TS_ERR_INVALID_ARG;
     }
     if (N > kNoAllocMaxN) {
@@ -96,7 +126,7 @@ extern "C" ts_status ts_make_screen_noalloc(const ts_medium* medium, const ts_gr
         return TS_ERR_INVALID_ARG;
     }
     unsigned char* base = nullptr;
-    ts_status st = scratch_for_current_device(&base);
+    ts_status st = scratch_for_current_context(&base);
     if (st != TS_OK) return st;
     float2* y = reinterpret_cast<float2*>(base + kOffY);
     float* g = reinterpret_cast<float*>(base + kOffG);

@@ -111,6 +111,27 @@ def test_buffers_are_checked_before_their_pointers_cross_the_abi():
             bd._need(torch.zeros(10, dtype=torch.float32, device="cuda"), "x", "float32", 11)
 
 
+def test_buffer_on_another_gpu_is_refused_before_its_pointer_crosses():
+    # a tensor on cuda:1 handed to a call that runs on cuda:0 (a plan's device, or the device of the
+    # call's other buffers) raises on the host; checked with stand-in tensors, so no GPU is needed
+    torch = pytest.importorskip("torch")
+    from unittest import mock
+
+    def fake(dev, dtype=torch.complex64, n=64):
+        t = mock.MagicMock(spec=torch.Tensor)
+        t.dtype, t.is_cuda, t.device = dtype, True, torch.device("cuda", dev)
+        t.numel.return_value = n
+        return t
+
+    bd._need(fake(0), "field", "complex64", 64, 0)  # same device passes
+    bd._need(fake(1), "field", "complex64", 64)  # no device asked for: not checked
+    with pytest.raises(ValueError, match="cuda:1.*cuda:0"):
+        bd._need(fake(1), "field", "complex64", 64, 0)
+    assert bd._device_of(fake(1), None, fake(1)) == 1
+    with pytest.raises(ValueError, match="different GPUs"):
+        bd._device_of(fake(0), fake(1))
+
+
 def test_every_plan_entry_point_refuses_a_null_handle_without_a_gpu():
     # the boundary's error convention: a NULL plan or batch handle is TS_ERR_INVALID_ARG, returned
     # before any CUDA call (so this runs on a machine without a GPU); destroying NULL is a no-op
@@ -128,8 +149,8 @@ def test_every_plan_entry_point_refuses_a_null_handle_without_a_gpu():
         "ts_evolve_screens": (N, 1, 0, 0, 0.9, 0.0, 0.0, 0.0, None, None, None, None, None),
         "ts_propagate": (N, None, 1, None, None, 1, 0, 0, 0, None, None, None),
         "ts_propagate_backward": (N, None, 1, None, None, 1, 0, 0, None),
-        "ts_moments_accumulate": (N, None, 1, 1, 0, None, None, None),
-        "ts_moments_finalize": (N, None, None, 1, 1, None, None, None, None),
+        "ts_moments_accumulate": (N, None, 1, 1, 0, None, None, None, None, None),
+        "ts_moments_finalize": (N, None, None, 1, 1, None, None, None, None, None, None),
         "ts_d2nn_forward": (N, None, 1, None, None, 0.3, None, 0, None, None, None, None),
         "ts_d2nn_backward": (N, 1, None, None, 0.3, None, 0, None, None, None, None, None, None),
         "ts_plan_timing": (N, 1, 4),

@@ -55,13 +55,19 @@ def test_receiver_forward_and_adjoint_match_oracle(kind):
         assert rel_l2(I[b].cpu().numpy(), Ib) < 1e-5
         Lb, dLdI = O.intensity_loss(Ib, Iref.astype(np.float64), kind, B * N * N)
         L_ref += Lb
-        mism[b] = np.sign(I[b].cpu().numpy() - Iref) != np.sign(Ib - Iref)
+        Ig = I[b].cpu().numpy()
+        mism[b] = np.sign(Ig - Iref) != np.sign(Ib - Iref)
+        if kind == 0:
+            # MAE: dL/dI = sign(I - Iref) is a decision; take it as the kernel does, from its FP32
+            # intensity, so both adjoints differentiate the same piecewise-linear loss.  A decision
+            # may differ from the FP64 one only where I lies within rounding of Iref.
+            _, dLdI = O.intensity_loss(Ig.astype(np.float64), Iref.astype(np.float64), 0, B * N * N)
+            assert np.all(np.abs(Ib - Iref)[mism[b]] <= 1e-5 * np.abs(Iref).max())
         gU_ref.append(O.d2nn_backward(A, th1.astype(np.float64), th2.astype(np.float64), Z1, W2, V, dLdI, rg1, rg2))
     assert abs(loss.item() / L_ref - 1) < 1e-6
     if kind == 0:
-        # MAE: dL/dI = sign(I - Iref) may flip where FP32 and FP64 intensities straddle Iref
-        assert mism.mean() < 1e-3
-    tol = 1e-4 if kind == 1 else 2e-2
+        assert mism.mean() < 1e-3  # decisions that differ from FP64 ones are rare
+    tol = 1e-4
     assert rel_l2(g1.cpu().numpy(), rg1) < tol
     assert rel_l2(g2.cpu().numpy(), rg2) < tol
     for b in range(B):

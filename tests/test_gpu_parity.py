@@ -54,7 +54,10 @@ def test_philox_words_bit_exact():
     assert [int(x) for x in out[:4].cpu().numpy().view(np.uint32)] == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
 
 
-@pytest.mark.parametrize("N,dx,sh,n_real,S", [(128, 2e-3, 0, 2, 5), (256, 1e-3, 3, 2, 3), (512, 1e-3, 3, 1, 2)])
+# the 1024- and 2048-point subharmonic cases span 1 and 2 m: the largest low-frequency amplitudes
+# relative to the grid term, where the per-pixel subharmonic sum's precision matters most
+@pytest.mark.parametrize("N,dx,sh,n_real,S", [(128, 2e-3, 0, 2, 5), (256, 1e-3, 3, 2, 3), (512, 1e-3, 3, 1, 2),
+                                             (1024, 1e-3, 3, 1, 2), (2048, 1e-3, 3, 1, 1)])
 def test_screens_match_oracle(N, dx, sh, n_real, S):
     dz, cn2 = [100.0] * S, [10 ** -13.5] * S  # below the Eq. 7 limit (165 m at N = 256, dx = 1 mm)
     plan = ts.Plan(LAM, N, dx, dz, cn2, l0=5e-3, L0=10.0, sh_levels=sh, max_batch=n_real)
@@ -269,8 +272,10 @@ def test_moments_and_beam_sums_match_oracle():
     plan.set_sources([0.0, 0.03])
     mean = torch.zeros((2, N, N), dtype=torch.float64, device=DEV)
     m2 = torch.zeros_like(mean)
+    acc = torch.zeros((2, 2), dtype=torch.float64, device=DEV)
     count = 0
     ref = [O.Welford((N, N)), O.Welford((N, N))]
+    ref_sums = np.zeros((2, 2))
     for chunk in range(2):
         B = R  # R/2 realizations x 2 sources
         U = cfield(B, N)
@@ -278,7 +283,7 @@ def test_moments_and_beam_sums_match_oracle():
         sums = torch.zeros((B, 2), dtype=torch.float64, device=DEV)
         plan.propagate(U, B, phi=None, phi_group=2, flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY, seed=seed,
                        real_base=chunk * (R // 2), intensity=I, beam_sums=sums)
-        plan.moments_accumulate(I, B, 2, count, mean, m2)
+        plan.moments_accumulate(I, B, 2, count, mean, m2, beam_sums=sums, beam_acc=acc)
         count += B // 2
         torch.cuda.synchronize()
         Ih = I.cpu().numpy().astype(np.float64)
@@ -291,12 +296,16 @@ def test_moments_and_beam_sums_match_oracle():
             sI, sR = O.beam_sums(N, dx, Iref)
             assert abs(sums[b, 0].item() / sI - 1) < 2 * TOL and abs(sums[b, 1].item() / sR - 1) < 2 * TOL
             ref[b % 2].update(Ih[b])  # same intensities: isolates the moment arithmetic
+            ref_sums[b % 2] += (sI, sR)
     si_map = torch.zeros_like(mean)
     si_mean = torch.zeros(2, dtype=torch.float64, device=DEV)
     si_c = torch.zeros(2, dtype=torch.float64, device=DEV)
-    plan.moments_finalize(mean, m2, 2, count, si_map=si_map, si_mean=si_mean, si_center=si_c)
+    w_lt = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.moments_finalize(mean, m2, 2, count, si_map=si_map, si_mean=si_mean, si_center=si_c, beam_acc=acc, w_lt=w_lt)
     torch.cuda.synchronize()
     for g in range(2):
+        # long-term radius from the oracle's beam sums over all realizations of the group (S23 / S24)
+        assert abs(w_lt[g].item() / np.sqrt(2 * ref_sums[g, 1] / ref_sums[g, 0]) - 1) < 2 * TOL
         assert rel_l2(mean[g].cpu().numpy(), ref[g].mean) < 1e-12
         assert rel_l2(m2[g].cpu().numpy(), ref[g].M2) < 1e-10
         si = ref[g].si_map()

@@ -62,8 +62,16 @@ def test_vacuum_second_moment_radius_is_the_beam_radius():
     I = torch.zeros((2, N, N), dtype=torch.float32, device=DEV)
     sums = torch.zeros((2, 2), dtype=torch.float64, device=DEV)
     plan.propagate(U, 2, flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY, intensity=I, beam_sums=sums)
+    # the same radius through the boundary's moment calls (one group, two realizations)
+    mean = torch.zeros((1, N, N), dtype=torch.float64, device=DEV)
+    m2 = torch.zeros_like(mean)
+    acc = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    w_lt = torch.zeros(1, dtype=torch.float64, device=DEV)
+    plan.moments_accumulate(I, 2, 1, 0, mean, m2, beam_sums=sums, beam_acc=acc)
+    plan.moments_finalize(mean, m2, 1, 2, beam_acc=acc, w_lt=w_lt)
     torch.cuda.synchronize()
     zR = np.pi * w0 ** 2 / LAM
     W = w0 * np.sqrt(1 + (L / zR) ** 2)
     wlt = np.sqrt(2 * sums[0, 1].item() / sums[0, 0].item())
     assert abs(wlt / W - 1) < 1e-4
+    assert abs(w_lt[0].item() / W - 1) < 1e-4

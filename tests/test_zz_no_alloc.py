@@ -48,6 +48,10 @@ def test_noalloc_screen_matches_plan_screens_on_two_calls():
         want = ref[real, screen].cpu().numpy().astype(np.float64)
         assert np.isfinite(got).all()
         assert rel_l2(got, want) < TOL
+        if screen == 2:  # and directly against the FP64 oracle for the first call
+            import oracle as O
+            md = O.medium(LAM, N, dx, l0=5e-3, L0=10.0)
+            assert rel_l2(got, O.make_screen(md, cn2[screen], dz[screen], 0, seed, screen, real)) < TOL
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -57,6 +61,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = lib.ts_make_screen_noalloc(C.byref(med), C.byref(bd.Grid(2048, 1e-3)), 100.0, 1e-15, 1, 0, 0,
                                     out.data_ptr(), None)
     assert st == 3 and b"exceeds" in lib.ts_last_error()
+    st = lib.ts_make_screen_noalloc(C.byref(med), C.byref(bd.Grid(300, 1e-3)), 100.0, 1e-15, 1, 0, 0,
+                                    out.data_ptr(), None)
+    assert st == 1 and b"128, 256, 512, 1024, 2048" in lib.ts_last_error()
     st = lib.ts_make_screen_noalloc(C.byref(med), C.byref(bd.Grid(256, 1e-3)), 100.0, 1e-15, 1, 64, 0,
                                     out.data_ptr(), None)
     assert st == 1
