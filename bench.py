@@ -406,9 +406,11 @@ def run_gpu(args):
         tc_plan.device_status()
         diff = (U.to(torch.complex128) - U_fp.to(torch.complex128)).abs().pow(2).sum(dim=(1, 2)).sqrt()
         rel = (diff / U_fp.to(torch.complex128).abs().pow(2).sum(dim=(1, 2)).sqrt()).cpu().tolist()
-        vs_oracle = None
+        # frames 0 and B - 1 of this step and the step's screens, for the CPU leg's FP64 oracle comparison
+        oracle_input = None
         if rank == 0 and not args.no_cpu:
-            vs_oracle = split_vs_oracle(wl, phasor, U, U_fp, frames=(0, B - 1))
+            oracle_input = (torch.angle(phasor.to(torch.complex128)).cpu().numpy(),
+                            {b: (U[b].cpu().numpy(), U_fp[b].cpu().numpy()) for b in (0, B - 1)})
         del U_fp
         n_tc = min(args.steps, 256)
         for _ in range(args.warmup):
@@ -439,7 +441,7 @@ def run_gpu(args):
                  "ms_per_step": round(ms_tc / n_tc, 5), "dtype": "bf16 hi+lo split, f32 accumulate",
                  "rel_l2_vs_fp32_per_frame_max": float(f"{max(rel):.3e}"),
                  "rel_l2_vs_fp32_per_frame": [float(f"{r:.3e}") for r in rel], "rel_l2_tolerance": 2e-3,
-                 "rel_l2_vs_oracle_per_frame": vs_oracle,
+                 "rel_l2_vs_oracle_per_frame": None,  # filled by the CPU leg below
                  "streams": tc_plan.tuning()[3], "kernels": tc_kernels,
                  "note": "same workload and screens, AR update + 16 screens + 8 beams per step; column and "
                          "row passes on tcgen05 (32 x 32 four-step DFT)"}
@@ -498,6 +500,8 @@ def run_gpu(args):
     }
     if rank == 0:
         res["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args.cpu_seconds)
+        if split is not None and oracle_input is not None:
+            split["rel_l2_vs_oracle_per_frame"] = oracle_field_errors(wl, *oracle_input)
         print(json.dumps(res), flush=True)
     if world > 1:
         dist.barrier()
@@ -507,24 +511,23 @@ def run_gpu(args):
 # ------------------------------------------------------------------------------------------------
 # CPU baseline / reference arm: the FP64 oracle as it stands, on one core and on all host cores
 # ------------------------------------------------------------------------------------------------
-def split_vs_oracle(wl, phasor, U_tc, U_fp, frames):
-    """Per-frame rel-L2 of the split-BF16 and FP32 receiver fields against the FP64 oracle propagated
-    through the same screens (phi = arg of the step's phasor screens) from the same Gaussian sources."""
+def oracle_field_errors(wl, phi, frames):
+    """CPU leg: per-frame rel-L2 of the split-BF16 and FP32 receiver fields (host copies) against the
+    FP64 oracle propagated through the same screens (phi = arg of the step's phasor screens) from the
+    same Gaussian sources."""
     import numpy as np
-    import torch
 
     import oracle as O
     from paper_2604_07248_gb300 import workloads as W
 
     t0 = time.perf_counter()
     md = O.medium(W.LAMBDA, wl.N, wl.dx, l0=W.L0_INNER, L0=W.L0_OUTER)
-    phi = torch.angle(phasor.to(torch.complex128)).cpu().numpy()
     out = {}
-    for b in frames:
+    for b, (u_tc, u_fp) in frames.items():
         ref = O.propagate(md, wl.dz, phi, O.source_gaussian(wl.N, wl.dx, wl.w0[b]))
         nr = np.linalg.norm(ref)
-        out[str(b)] = {"split_bf16": float(f"{np.linalg.norm(U_tc[b].cpu().numpy() - ref) / nr:.3e}"),
-                       "fp32": float(f"{np.linalg.norm(U_fp[b].cpu().numpy() - ref) / nr:.3e}")}
+        out[str(b)] = {"split_bf16": float(f"{np.linalg.norm(u_tc - ref) / nr:.3e}"),
+                       "fp32": float(f"{np.linalg.norm(u_fp - ref) / nr:.3e}")}
     out["oracle_seconds"] = round(time.perf_counter() - t0, 1)
     return out
 
@@ -704,7 +707,8 @@ def run_uneven(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "uneven batch: 64 instances", "instances_by_N": counts,
-                      "field_screen_steps_per_step": units, "batch": batch.info(), "status": status},
+                      "field_screen_steps_per_step": units, "batch": batch.info(), "status": status,
+                      "autotune": batch.tuning()},
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
                         "scope": "whole step (screen synthesis + the persistent launch), algorithmic bytes / time",
@@ -779,6 +783,7 @@ def run_monte_carlo(args):
         sig_r2 = 1.23 * c * (2 * 3.141592653589793 / W.LAMBDA) ** (7 / 6) * wl.L ** (11 / 6)
         si[f"{c:.3g}"] = {"realizations": count[i], "sigma_R2": round(sig_r2, 4),
                           "SI_plane_grid_mean": round(float(sm[0].item()), 4)}
+    validation = mc_validation(plans, cn2s, wl, ph, U, I, sums, Rc, dev)
     units = args.steps * B * S * world
     step_bytes = (screen_bytes(N, Rc * S) + propagate_bytes(N, B, S, 2, intensity_only=True)
                   + N * N * (4 * B + 2 * 32))  # moments: intensities read, FP64 mean + M2 read + write
@@ -798,9 +803,99 @@ def run_monte_carlo(args):
                         "frac": round(gbs / peak, 4), "traffic": None, "peak_source": peak_src,
                         "scope": "whole step (all kernels), algorithmic bytes per step / device time per step",
                         "algorithmic_bytes_per_step": int(step_bytes)},
-           "si": si}
+           "si": si, "validation": validation}
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def mc_theory(cn2, wl, sh_levels):
+    """Theory for the Monte Carlo workload's discrete model (numpy, from the phase PSD of S14 / S17 and
+    the subharmonic cells of Eq. 2): the continuous sigma_R^2 (S19), the plane wave's first-order
+    Rytov SI for thin screens (a screen d before the receiver adds 4 sum s^2 sin^2(kappa^2 d / 2k)),
+    the 2 cm beam's long-term radius from the moment theorem (a screen adds its mean-square gradient
+    / k^2 to the mean-square angle: W_LT^2 = W(L)^2 + 2 sum (d / k)^2 sum kappa^2 s^2), and Andrews'
+    weak-turbulence W_LT = W sqrt(1 + 1.33 sigma_R^2 Lambda^(5/6))."""
+    import numpy as np
+
+    from paper_2604_07248_gb300 import workloads as W
+
+    k = 2 * np.pi / W.LAMBDA
+    N, dx, L, S = wl.N, wl.dx, wl.L, wl.S
+    dz = L / S
+    dk = 2 * np.pi / (N * dx)
+    k0sq, kmsq = (2 * np.pi / W.L0_OUTER) ** 2, (2 * np.pi / W.L0_INNER) ** 2
+
+    def phi_phi(kap2):
+        return 2 * np.pi * k * k * dz * 0.033 * cn2 * (kap2 + k0sq) ** (-11 / 6) * np.exp(-kap2 / kmsq)
+
+    f = np.fft.fftfreq(N, 1 / N) * dk
+    k2 = f[None, :] ** 2 + f[:, None] ** 2
+    s2 = phi_phi(k2) * dk * dk
+    s2[0, 0] = 0.0
+    d = [L - s * dz for s in range(1, S + 1)]
+    rytov = float(sum(4 * np.sum(s2 * np.sin(k2 * ds / (2 * k)) ** 2) for ds in d))
+    grad2 = float(np.sum(k2 * s2))
+    if sh_levels:
+        for p in range(1, 4):
+            for m in (-1, 0, 1):
+                for n in (-1, 0, 1):
+                    if m or n:
+                        kk = (m * m + n * n) * (dk / 3 ** p) ** 2
+                        grad2 += kk * phi_phi(kk) * (dk / 3 ** p) ** 2
+    zR = np.pi * 0.02 ** 2 / W.LAMBDA
+    Wv = 0.02 * np.sqrt(1 + (L / zR) ** 2)
+    sig_r2 = 1.23 * cn2 * k ** (7 / 6) * L ** (11 / 6)
+    lam_ = 2 * L / (k * Wv ** 2)
+    return {"sigma_R2": round(sig_r2, 5), "SI_rytov_discrete": round(rytov, 5),
+            "W_LT_moment_m": round(float(np.sqrt(Wv ** 2 + 2 * sum((ds / k) ** 2 for ds in d) * grad2)), 6),
+            "W_LT_andrews_m": round(float(Wv * np.sqrt(1 + 1.33 * sig_r2 * lam_ ** (5 / 6))), 6),
+            "W_vacuum_m": round(float(Wv), 6)}
+
+
+def mc_validation(plans, cn2s, wl, ph, U, I, sums, Rc, dev, R=1024):
+    """R realizations per Cn^2 through the configured plans (subharmonics): the 2 cm beam's W_LT and
+    on-axis SI; and through plans without subharmonics (periodic screens): the plane wave's SI over the
+    grid against the discrete Rytov sum.  The configured subharmonic screens are not periodic, so on
+    the periodic grid a plane wave picks up seam scintillation; that SI is listed as well."""
+    import torch
+
+    import paper_2604_07248_gb300 as ts
+    from paper_2604_07248_gb300 import workloads as W
+
+    N, S = wl.N, wl.S
+    B = 2 * Rc
+    out = {}
+    for i, c in enumerate(cn2s):
+        row = mc_theory(c, wl, 3)
+        nosh = ts.Plan(W.LAMBDA, N, wl.dx, wl.dz, [c] * S, l0=W.L0_INNER, L0=W.L0_OUTER, max_batch=B)
+        nosh.set_sources([0.0, 0.02])
+        for tag, p in (("sh3", plans[i]), ("sh0", nosh)):
+            mean = torch.zeros((2, N, N), dtype=torch.float64, device=dev)
+            m2 = torch.zeros_like(mean)
+            acc = torch.zeros((2, 2), dtype=torch.float64, device=dev)
+            count = 0
+            for ch in range(R // Rc):
+                p.make_screens(None, wl.seed, real_base=900000 + i * 10000 + ch * Rc, n_real=Rc, phasor=ph)
+                p.propagate(U, B, phasor=ph, phi_group=2,
+                            flags=ts.TS_PROP_SOURCE | ts.TS_PROP_INTENSITY | ts.TS_PROP_NO_FIELD, intensity=I,
+                            beam_sums=sums)
+                p.moments_accumulate(I, B, 2, count, mean, m2, beam_sums=sums, beam_acc=acc)
+                count += Rc
+            sm = torch.zeros(2, dtype=torch.float64, device=dev)
+            sc = torch.zeros(2, dtype=torch.float64, device=dev)
+            w = torch.zeros(2, dtype=torch.float64, device=dev)
+            p.moments_finalize(mean, m2, 2, count, si_mean=sm, si_center=sc, beam_acc=acc, w_lt=w)
+            torch.cuda.synchronize(dev)
+            if tag == "sh3":
+                row.update({"W_LT_m": round(float(w[1].item()), 6), "SI_gauss_axis": round(float(sc[1].item()), 5),
+                            "SI_plane_grid_with_subharmonic_seam": round(float(sm[0].item()), 5)})
+            else:
+                row.update({"SI_plane_grid_periodic_screens": round(float(sm[0].item()), 5),
+                            "SI_gauss_axis_periodic_screens": round(float(sc[1].item()), 5)})
+        nosh.close()
+        row["realizations"] = R
+        out[f"{c:.3g}"] = row
+    return out
 
 
 def run_d2nn(args):
