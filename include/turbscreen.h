@@ -409,13 +409,28 @@ typedef struct {
 
 #define TS_BATCH_TEST_STALL 1 /* test hook: instance 0 waits for a tile that never completes, so its
                                  dependency wait runs out and the batch reports TS_ERR_DEVICE_TIMEOUT */
+#define TS_BATCH_NO_TUNE 2    /* keep the default tile shapes and item order (no autotuning)        */
 
 /* Builds a batch: validates the instances (all plans on the current device, separable transfer
  * form), lays out the work list (instance, phase, tile) by increasing phase, allocates the screen
  * workspace for instances without screens, and captures the run (screen synthesis, counter reset,
  * one persistent launch) as a CUDA graph.  timeout_s bounds every device-side dependency wait.
+ * Unless TS_BATCH_NO_TUNE (or the stall hook) is given, an autotuner first chooses the tile shape of
+ * every grid size -- the points per thread of its line FFTs, hence the rows of a row tile and the
+ * columns of a column tile: N = 512 and 2048 at 32 or 16, N = 1024 at 32, N <= 256 at 16 -- and the
+ * order of instances within a phase (as given, or largest grids first), by timing whole replays of
+ * the batch on scratch fields it allocates for the purpose and frees (the callers' fields are not
+ * touched); ts_batch_tuning reports the choices.  The call synchronises the device.
  * Copies `inst`; the plans, fields and screens must outlive the batch. */
 ts_status ts_batch_create(ts_batch* batch, const ts_batch_instance* inst, int n, double timeout_s, int flags);
+
+/* The batch autotuner's choices: for each distinct grid size of the batch (ascending, at most 5,
+ * written to sizes[]) the points per thread of its tiles; the item order (0 = instances in the
+ * caller's order within a phase, 1 = largest grids first); the number of configurations timed (0 when
+ * not tuned); and the replay times (us) of the default configuration and of the chosen one.  Output
+ * pointers may be NULL.  Host-only. */
+ts_status ts_batch_tuning(ts_batch batch, int* n_sizes, int* sizes, int* points_per_thread, int* order,
+                          int* candidates, float* us_default, float* us_chosen);
 
 /* Launches the captured graph on `stream` (asynchronous). */
 ts_status ts_batch_run(ts_batch batch, void* stream);

@@ -6,11 +6,11 @@ around the propagate/adjoint pair.  PyTorch supplies device memory and streams o
 """
 from __future__ import annotations
 
-from .binding import (TS_BATCH_TEST_STALL, TS_PLAN_ALLOW_ALIASING, TS_PLAN_SPLIT_BF16, TS_PLAN_TEST_STALL, TS_PROP_INTENSITY,
+from .binding import (TS_BATCH_NO_TUNE, TS_BATCH_TEST_STALL, TS_PLAN_ALLOW_ALIASING, TS_PLAN_SPLIT_BF16, TS_PLAN_TEST_STALL, TS_PROP_INTENSITY,
                       TS_PROP_NO_FIELD, TS_PROP_SOURCE, Batch, Plan, TsError, cn2_hufnagel_valley, load, max_step,
                       philox4x32_10, place_screens, power_law_constant, rytov_interval)
 
-__all__ = ["Plan", "Batch", "TsError", "TS_BATCH_TEST_STALL", "load", "max_step", "philox4x32_10", "propagate",
+__all__ = ["Plan", "Batch", "TsError", "TS_BATCH_NO_TUNE", "TS_BATCH_TEST_STALL", "load", "max_step", "philox4x32_10", "propagate",
            "cn2_hufnagel_valley", "rytov_interval", "place_screens", "power_law_constant", "TS_PROP_SOURCE",
            "TS_PROP_INTENSITY", "TS_PROP_NO_FIELD", "TS_PLAN_ALLOW_ALIASING", "TS_PLAN_SPLIT_BF16",
            "TS_PLAN_TEST_STALL"]

@@ -40,6 +40,7 @@ class BatchInstance(C.Structure):
 
 
 TS_BATCH_TEST_STALL = 1
+TS_BATCH_NO_TUNE = 2
 
 
 class Medium(C.Structure):
@@ -94,6 +95,8 @@ SIGNATURES = {
     "ts_batch_run": (_I, [_P, _P]),
     "ts_batch_status": (_I, [_P, _P]),
     "ts_batch_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "ts_batch_tuning": (_I, [_P, C.POINTER(C.c_int), _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "ts_batch_destroy": (_I, [_P]),
     "ts_status_string": (C.c_char_p, [_I]),
     "ts_last_error": (C.c_char_p, []),
@@ -550,6 +553,18 @@ class Batch:
         """0, or the TS_ERR_* code the device reported (does not raise)."""
         with _on(self.device):
             return load().ts_batch_status(self._h, _stream(stream, self.device))
+
+    def tuning(self):
+        """The autotuner's choices: {N: points per thread}, item order, configurations timed, replay
+        time of the default and of the chosen configuration (us)."""
+        n, order, cand = C.c_int(), C.c_int(), C.c_int()
+        sizes, ppt = (C.c_int * 5)(), (C.c_int * 5)()
+        d, c = C.c_float(), C.c_float()
+        _check(load().ts_batch_tuning(self._h, C.byref(n), sizes, ppt, C.byref(order), C.byref(cand), C.byref(d),
+                                      C.byref(c)), "ts_batch_tuning")
+        return {"points_per_thread": {int(sizes[i]): int(ppt[i]) for i in range(n.value)},
+                "order": "largest grids first" if order.value == 1 else "caller's order",
+                "candidates": cand.value, "us_default": round(d.value, 1), "us_chosen": round(c.value, 1)}
 
     def info(self):
         n, g, b = C.c_int(), C.c_int(), C.c_size_t()

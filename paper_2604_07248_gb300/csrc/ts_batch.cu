@@ -11,6 +11,7 @@
 // a clock64 budget: a CTA that gives up sets the error word, every CTA then stops taking work, and the
 // host reads the status with ts_batch_status.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,6 +26,7 @@ constexpr int kBatchThreads = 256;
 
 struct BInst {
     int N, S, src;
+    int E;  // points per thread of this instance's tiles (the batch autotuner's choice for its N)
     int tiles_row, tiles_col;
     int ctr_base;
     int extra_need;  // test hook: added to the phase-1 dependency of this instance (never satisfied)
@@ -32,7 +34,7 @@ struct BInst {
     float dk;
     float2* field;
     const float2* phasor;  // [S][N][N]
-    const float2* tw;      // twiddles for the default points-per-thread of N
+    const float2* tw;      // twiddles for E points per thread
     const float2* P;       // [S][N] separable per-axis transfer factors
     const float* ccross;   // [S] dz / (4 k^3)
 };
@@ -61,7 +63,7 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
     return v;
 }
 
-template <int N>
+template <int N, int E>
 __device__ __noinline__ void batch_row(const BInst& I, int phase, int tile, float2* smem, bool stage)
 {
     RowParams a{};
@@ -72,17 +74,17 @@ __device__ __noinline__ void batch_row(const BInst& I, int phase, int tile, floa
     a.n_src = 1;
     a.src_coef[0] = I.src_coef;
     if (phase == 0) {
-        if (I.src) row_tile<N, 0, RP_IN_SOURCE | RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
-        else row_tile<N, 0, RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
+        if (I.src) row_tile<N, E, RP_IN_SOURCE | RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
+        else row_tile<N, E, RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
         return;
     }
     const int s = phase / 2 - 1;
     a.phasor = I.phasor + (size_t)s * N * N;
-    if (s < I.S - 1) row_tile<N, 0, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
-    else row_tile<N, 0, RP_IN_FREQ | RP_PHASOR | RP_STORE>(a, tile, 0, smem, stage);
+    if (s < I.S - 1) row_tile<N, E, RP_IN_FREQ | RP_PHASOR | RP_OUT_FREQ | RP_STORE>(a, tile, 0, smem, stage);
+    else row_tile<N, E, RP_IN_FREQ | RP_PHASOR | RP_STORE>(a, tile, 0, smem, stage);
 }
 
-template <int N>
+template <int N, int E>
 __device__ __noinline__ void batch_col(const BInst& I, int phase, int tile, float2* smem, bool stage)
 {
     const int s = (phase - 1) / 2;
@@ -92,14 +94,14 @@ __device__ __noinline__ void batch_col(const BInst& I, int phase, int tile, floa
     c.P = I.P + (size_t)s * N;
     c.ccross = I.ccross[s];
     c.dk = I.dk;
-    col_tile<N, 0, false, true>(c, tile, 0, smem, stage);
+    col_tile<N, E, false, true>(c, tile, 0, smem, stage);
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchParams bp)
 {
     extern __shared__ float2 smem[];
     __shared__ int s_item;
-    int lastN = 0;
+    int last = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             int it = atomicAdd(bp.head, 1);
@@ -133,16 +135,24 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchPara
         if (it < 0) break;
         const int4 w = bp.items[it];
         const BInst& I = bp.inst[w.x];
-        const bool stage = I.N != lastN;  // twiddles depend only on N (same points per thread)
-        lastN = I.N;
+        const int key = I.N * 64 + I.E;
+        const bool stage = key != last;  // twiddles depend only on N and the points per thread
+        last = key;
         const bool colpass = (w.y & 1) != 0;
-        switch (I.N) {
-        case 128: colpass ? batch_col<128>(I, w.y, w.z, smem, stage) : batch_row<128>(I, w.y, w.z, smem, stage); break;
-        case 256: colpass ? batch_col<256>(I, w.y, w.z, smem, stage) : batch_row<256>(I, w.y, w.z, smem, stage); break;
-        case 512: colpass ? batch_col<512>(I, w.y, w.z, smem, stage) : batch_row<512>(I, w.y, w.z, smem, stage); break;
-        case 1024: colpass ? batch_col<1024>(I, w.y, w.z, smem, stage) : batch_row<1024>(I, w.y, w.z, smem, stage); break;
-        default: colpass ? batch_col<2048>(I, w.y, w.z, smem, stage) : batch_row<2048>(I, w.y, w.z, smem, stage); break;
+#define TS_BATCH_CASE(NN, EE)                                                                     \
+    case NN * 64 + EE:                                                                            \
+        colpass ? batch_col<NN, EE>(I, w.y, w.z, smem, stage) : batch_row<NN, EE>(I, w.y, w.z, smem, stage); \
+        break;
+        switch (key) {
+            TS_BATCH_CASE(128, 16)
+            TS_BATCH_CASE(256, 16)
+            TS_BATCH_CASE(512, 16)
+            TS_BATCH_CASE(512, 32)
+            TS_BATCH_CASE(1024, 32)
+            TS_BATCH_CASE(2048, 16)
+        default: colpass ? batch_col<2048, 32>(I, w.y, w.z, smem, stage) : batch_row<2048, 32>(I, w.y, w.z, smem, stage);
         }
+#undef TS_BATCH_CASE
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -151,11 +161,33 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchPara
     }
 }
 
-template <int N>
+template <int N, int E>
 constexpr size_t batch_smem_n()
 {
-    return RowCfg<N, 0>::smem > ColCfg<N, 0>::smem ? RowCfg<N, 0>::smem : ColCfg<N, 0>::smem;
+    static_assert(ColCfg<N, E>::THREADS == kBatchThreads, "a column tile takes the batch kernel's 256 threads");
+    return RowCfg<N, E>::smem > ColCfg<N, E>::smem ? RowCfg<N, E>::smem : ColCfg<N, E>::smem;
 }
+
+// shared memory of one (N, points per thread) tile shape; 0 for shapes the batch kernel does not take
+size_t batch_smem(int N, int E)
+{
+    switch (N * 64 + E) {
+    case 128 * 64 + 16: return batch_smem_n<128, 16>();
+    case 256 * 64 + 16: return batch_smem_n<256, 16>();
+    case 512 * 64 + 16: return batch_smem_n<512, 16>();
+    case 512 * 64 + 32: return batch_smem_n<512, 32>();
+    case 1024 * 64 + 32: return batch_smem_n<1024, 32>();
+    case 2048 * 64 + 16: return batch_smem_n<2048, 16>();
+    case 2048 * 64 + 32: return batch_smem_n<2048, 32>();
+    default: return 0;
+    }
+}
+
+// the tile shapes the autotuner may choose per N (points per thread; the first is the default)
+constexpr int kSizes = 5;  // N = 128, 256, 512, 1024, 2048
+inline int size_index(int N) { return N == 128 ? 0 : N == 256 ? 1 : N == 512 ? 2 : N == 1024 ? 3 : 4; }
+constexpr int kDefaultE[kSizes] = {16, 16, 32, 32, 32};
+constexpr int kAltE[kSizes] = {0, 0, 16, 0, 16};  // 0: no alternative (N = 1024 at 16 points needs 512 threads)
 
 }  // namespace
 
@@ -179,9 +211,21 @@ struct Batch {
     std::vector<uint32_t> real;
     long long budget = 0;
     cudaStream_t cap = nullptr;
+    // the screen syntheses are captured on kSynthStreams forked streams (graph branches that run
+    // concurrently); instances of one plan share its workspace and therefore one branch
+    static constexpr int kSynthStreams = 4;
+    cudaStream_t synth[kSynthStreams] = {};
+    cudaEvent_t fork = nullptr, join[kSynthStreams] = {};
+    std::vector<int> branch;  // branch of each instance
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t bytes = 0;
+    size_t items_cap = 0;        // int4 entries allocated for the work list
+    // autotuner: points per thread per N (index size_index(N)), item order, what it timed
+    int e_of[kSizes] = {16, 16, 32, 32, 32};
+    int order = 0;               // 0: instances in the caller's order within a phase; 1: largest N first
+    int candidates = 0;          // configurations timed (0: not tuned)
+    float us_default = 0.0f, us_chosen = 0.0f;
 };
 
 }  // namespace ts
@@ -201,16 +245,23 @@ void free_batch(Batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < Batch::kSynthStreams; ++k) {
+        if (b->synth[k]) cudaStreamDestroy(b->synth[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     void* ptrs[] = {b->inst, b->items, b->counters, b->ccross, b->screens};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete b;
 }
 
-// the launch sequence captured into the batch's graph: screen synthesis, counter reset, one launch
+// the launch sequence captured into the batch's graph: screen synthesis (on forked branches), counter
+// reset, one launch
 cudaError_t record_batch(Batch& b, cudaStream_t st)
 {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(b.fork, st);
+    for (int k = 0; k < Batch::kSynthStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b.synth[k], b.fork, 0);
     for (int i = 0; i < b.n && e == cudaSuccess; ++i) {
         if (!b.gen[i]) continue;
         Plan& p = *b.plans[i];
@@ -221,7 +272,11 @@ cudaError_t record_batch(Batch& b, cudaStream_t st)
         a.r_begin = b.real[i];
         a.items = p.S;
         a.phasor = b.screens + b.screen_off[i];
-        e = launch_screens(p, SC_INDEP, a, st);
+        e = launch_screens(p, SC_INDEP, a, b.synth[b.branch[i]]);
+    }
+    for (int k = 0; k < Batch::kSynthStreams && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b.join[k], b.synth[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b.join[k], 0);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(b.counters, 0, sizeof(int) * b.n_counters, st);
     if (e == cudaSuccess) {
@@ -235,6 +290,157 @@ cudaError_t record_batch(Batch& b, cudaStream_t st)
         bp.budget = b.budget;
         batch_kernel<<<b.grid, kBatchThreads, b.smem, st>>>(bp);
         e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Instance descriptors and work list of one configuration: the points per thread of every N
+// (b.e_of) and the order of instances within a phase (b.order).  Items stay sorted by phase, so the
+// schedule cannot deadlock whatever the order within a phase.
+void lay_out(Batch& b, std::vector<int4>& items)
+{
+    items.clear();
+    size_t smem = 0;
+    for (int i = 0; i < b.n; ++i) {
+        BInst& bi = b.host_inst[i];
+        const Plan& p = *b.plans[i];
+        bi.E = b.e_of[size_index(bi.N)];
+        const int T = bi.N / bi.E;
+        bi.tiles_row = bi.N / (kBatchThreads / T);
+        bi.tiles_col = bi.N / (kBatchThreads / T);
+        bi.tw = (bi.E == 16 && bi.N >= 512) ? p.tw16 : p.tw;
+        smem = std::max(smem, batch_smem(bi.N, bi.E));
+    }
+    std::vector<int> seq(b.n);
+    for (int i = 0; i < b.n; ++i) seq[i] = i;
+    if (b.order == 1)
+        std::stable_sort(seq.begin(), seq.end(), [&](int x, int y) { return b.host_inst[x].N > b.host_inst[y].N; });
+    int max_phase = 0;
+    for (int i = 0; i < b.n; ++i) max_phase = std::max(max_phase, 2 * b.host_inst[i].S);
+    for (int k = 0; k <= max_phase; ++k)
+        for (int i : seq) {
+            const BInst& bi = b.host_inst[i];
+            if (k > 2 * bi.S) continue;
+            const int tiles = (k & 1) ? bi.tiles_col : bi.tiles_row;
+            for (int t = 0; t < tiles; ++t) items.push_back(make_int4(i, k, t, 0));
+        }
+    b.n_items = (int)items.size();
+    b.smem = smem;
+}
+
+// Uploads the descriptors and the work list, sizes the persistent grid and captures the graph
+// (screen synthesis, counter reset, one launch) on the batch's private stream.
+cudaError_t install(Batch& b, const std::vector<int4>& items)
+{
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    if (items.size() > b.items_cap) {
+        if (b.items) ok(cudaFree(b.items));
+        b.items = nullptr;
+        ok(cudaMalloc(&b.items, sizeof(int4) * items.size()));
+        b.items_cap = items.size();
+    }
+    ok(cudaMemcpy(b.inst, b.host_inst.data(), sizeof(BInst) * b.n, cudaMemcpyHostToDevice));
+    ok(cudaMemcpy(b.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    int sms = 0, per_sm = 0;
+    ok(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem));
+    ok(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+    ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b.smem));
+    b.grid = std::max(1, sms * std::max(1, per_sm));  // as many CTAs as fit at once
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.graph) cudaGraphDestroy(b.graph);
+    b.exec = nullptr;
+    b.graph = nullptr;
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = record_batch(b, b.cap);
+            e = cudaStreamEndCapture(b.cap, &b.graph);
+            if (e == cudaSuccess) e = er;
+        }
+    }
+    ok(b.graph ? cudaGraphInstantiate(&b.exec, b.graph, 0) : cudaErrorInvalidValue);
+    return e;
+}
+
+// Device time of one replay of the installed graph (us, best of `rounds` replays), or a negative
+// value when a dependency wait of the run ran out.
+cudaError_t time_installed(Batch& b, int rounds, float* us)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, b.cap);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b.exec, b.cap);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b.cap);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) best = std::min(best, ms * 1000.0f);
+    }
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, b.counters + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *us = err != 0 ? -1.0f : best;
+    return e;
+}
+
+// The batch autotuner: times whole replays of the batch on scratch fields (the callers' fields are
+// not touched), first the default tile shapes, then each N's alternative points per thread one N at
+// a time (kept when faster), then the other item order; three interleaved replays per candidate.
+cudaError_t autotune_batch(Batch& b, std::vector<int4>& items)
+{
+    std::vector<float2*> scratch(b.n, nullptr), real(b.n);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b.n && e == cudaSuccess; ++i) {
+        real[i] = b.host_inst[i].field;
+        const size_t n2 = (size_t)b.host_inst[i].N * b.host_inst[i].N;
+        e = cudaMalloc(&scratch[i], sizeof(float2) * n2);
+        if (e == cudaSuccess) e = cudaMemset(scratch[i], 0, sizeof(float2) * n2);
+        if (e == cudaSuccess) b.host_inst[i].field = scratch[i];
+    }
+    auto measure = [&](float* us) -> cudaError_t {
+        lay_out(b, items);
+        cudaError_t x = install(b, items);
+        if (x == cudaSuccess) x = time_installed(b, 1, us);  // warm-up replay
+        if (x == cudaSuccess) x = time_installed(b, 3, us);
+        return x;
+    };
+    bool present[kSizes] = {};
+    for (int i = 0; i < b.n; ++i) present[size_index(b.host_inst[i].N)] = true;
+    float best = 0.0f;
+    if (e == cudaSuccess) e = measure(&best);
+    b.candidates = 1;
+    b.us_default = best;
+    for (int k = 0; k < kSizes && e == cudaSuccess; ++k) {
+        if (!present[k] || kAltE[k] == 0) continue;
+        const int keep = b.e_of[k];
+        b.e_of[k] = kAltE[k];
+        float us = 0.0f;
+        e = measure(&us);
+        ++b.candidates;
+        if (e == cudaSuccess && !(us > 0.0f && (best <= 0.0f || us < best))) b.e_of[k] = keep;
+        else if (e == cudaSuccess) best = us;
+    }
+    if (e == cudaSuccess) {
+        b.order = 1;
+        float us = 0.0f;
+        e = measure(&us);
+        ++b.candidates;
+        if (e == cudaSuccess && !(us > 0.0f && (best <= 0.0f || us < best))) b.order = 0;
+        else if (e == cudaSuccess) best = us;
+    }
+    b.us_chosen = best;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b.cap);
+    for (int i = 0; i < b.n; ++i) {
+        b.host_inst[i].field = real[i];
+        if (scratch[i]) cudaFree(scratch[i]);
     }
     return e;
 }
@@ -253,8 +459,6 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
     cudaError_t e = cudaGetDevice(&b->device);
     size_t screen_elems = 0;
     int ctr = 0;
-    std::vector<int4> items;
-    int max_phase = 0;
     std::vector<float> ccross;
     std::vector<size_t> cc_off;
     for (int i = 0; i < n; ++i) {
@@ -287,16 +491,12 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
         bi.N = N;
         bi.S = p->S;
         bi.src = inst[i].source ? 1 : 0;
-        const int T = N / (N <= 256 ? 16 : 32);
-        bi.tiles_row = N / (kBatchThreads / T);
-        bi.tiles_col = N / (kBatchThreads / T);
         bi.ctr_base = ctr;
         ctr += 2 * p->S + 1;
         bi.extra_need = ((flags & TS_BATCH_TEST_STALL) && i == 0) ? 1 : 0;
         bi.src_coef = p->src_coef[0];
         bi.dk = (float)p->dk;
         bi.field = reinterpret_cast<float2*>(inst[i].field);
-        bi.tw = p->tw;
         bi.P = p->P;
         bi.phasor = reinterpret_cast<const float2*>(inst[i].phasor);
         b->gen.push_back(inst[i].phasor ? 0 : 1);
@@ -307,36 +507,12 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
         cc_off.push_back(ccross.size());
         for (int s = 0; s < p->S; ++s) ccross.push_back((float)(p->dz[s] / (4.0 * p->k * p->k * p->k)));
         b->host_inst.push_back(bi);
-        max_phase = std::max(max_phase, 2 * p->S);
     }
-    // Items by increasing phase, instances and tiles interleaved within a phase (a topological order,
-    // so the schedule cannot deadlock).  Staggering instances by a few phases was measured slower.
-    for (int k = 0; k <= max_phase; ++k)
-        for (int i = 0; i < n; ++i) {
-            const BInst& bi = b->host_inst[i];
-            if (k > 2 * bi.S) continue;
-            const int tiles = (k & 1) ? bi.tiles_col : bi.tiles_row;
-            for (int t = 0; t < tiles; ++t) items.push_back(make_int4(i, k, t, 0));
-        }
-    b->n_items = (int)items.size();
     b->n_counters = 2 + ctr;
-    // shared memory: the largest tile of any instance
-    size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
-        switch (b->host_inst[i].N) {
-        case 128: smem = std::max(smem, batch_smem_n<128>()); break;
-        case 256: smem = std::max(smem, batch_smem_n<256>()); break;
-        case 512: smem = std::max(smem, batch_smem_n<512>()); break;
-        case 1024: smem = std::max(smem, batch_smem_n<1024>()); break;
-        default: smem = std::max(smem, batch_smem_n<2048>()); break;
-        }
-    }
-    b->smem = smem;
     auto ok = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
     };
     ok(cudaMalloc(&b->inst, sizeof(BInst) * n));
-    ok(cudaMalloc(&b->items, sizeof(int4) * items.size()));
     ok(cudaMalloc(&b->counters, sizeof(int) * b->n_counters));
     ok(cudaMalloc(&b->ccross, sizeof(float) * std::max<size_t>(1, ccross.size())));
     if (screen_elems) ok(cudaMalloc(&b->screens, sizeof(float2) * screen_elems));
@@ -346,39 +522,84 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
             bi.ccross = b->ccross + cc_off[i];
             if (!bi.phasor) bi.phasor = b->screens + b->screen_off[i];
         }
-        ok(cudaMemcpy(b->inst, b->host_inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice));
-        ok(cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(b->ccross, ccross.data(), sizeof(float) * ccross.size(), cudaMemcpyHostToDevice));
         ok(cudaMemset(b->counters, 0, sizeof(int) * b->n_counters));
     }
-    b->bytes = sizeof(BInst) * n + sizeof(int4) * items.size() + sizeof(int) * b->n_counters +
-               sizeof(float) * ccross.size() + sizeof(float2) * screen_elems;
-    // grid: as many CTAs as fit at once (one per SM at this shared-memory size and up to the limit)
-    int sms = 0, per_sm = 0, clock_khz = 0;
-    ok(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    ok(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    int clock_khz = 0;
     ok(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, b->device));
-    ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem));
-    b->grid = std::max(1, sms * std::max(1, per_sm));
     b->budget = (long long)(timeout_s * (double)std::max(clock_khz, 1000000) * 1e3);
-    // capture the whole run as one graph on a private stream
     ok(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-    if (e == cudaSuccess) {
-        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t er = record_batch(*b, b->cap);
-            e = cudaStreamEndCapture(b->cap, &b->graph);
-            if (e == cudaSuccess) e = er;
+    for (int k = 0; k < Batch::kSynthStreams; ++k) {
+        ok(cudaStreamCreateWithFlags(&b->synth[k], cudaStreamNonBlocking));
+        ok(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+    }
+    ok(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    {
+        // synthesis branches: each plan on the branch with the least screen work so far (largest first)
+        std::vector<int> order(n);
+        for (int i = 0; i < n; ++i) order[i] = i;
+        auto work = [&](int i) { return (double)b->host_inst[i].S * b->host_inst[i].N * b->host_inst[i].N; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+        double load[Batch::kSynthStreams] = {};
+        std::vector<std::pair<const Plan*, int>> placed;
+        b->branch.assign(n, 0);
+        for (int i : order) {
+            int br = -1;
+            for (auto& pp : placed)
+                if (pp.first == b->plans[i]) br = pp.second;
+            if (br < 0) {
+                br = (int)(std::min_element(load, load + Batch::kSynthStreams) - load);
+                placed.push_back({b->plans[i], br});
+            }
+            b->branch[i] = br;
+            if (b->gen[i]) load[br] += work(i);
         }
     }
-    ok(b->graph ? cudaGraphInstantiate(&b->exec, b->graph, 0) : cudaErrorInvalidValue);
+    std::vector<int4> items;
+    // tile shapes and item order: timed by the autotuner on scratch fields, unless the caller pins
+    // the defaults (or drives the stall test, whose every replay would time out); TS_BATCH_E=16 pins
+    // the 16-point tiles wherever a grid size has them (tests of those tiles)
+    const char* force = std::getenv("TS_BATCH_E");
+    if (force && std::atoi(force) == 16) {
+        for (int k = 0; k < kSizes; ++k)
+            if (kAltE[k]) b->e_of[k] = kAltE[k];
+    } else if (e == cudaSuccess && !(flags & (TS_BATCH_NO_TUNE | TS_BATCH_TEST_STALL))) {
+        ok(autotune_batch(*b, items));
+    }
+    if (e == cudaSuccess) {
+        lay_out(*b, items);
+        ok(install(*b, items));
+    }
+    b->bytes = sizeof(BInst) * n + sizeof(int4) * b->items_cap + sizeof(int) * b->n_counters +
+               sizeof(float) * ccross.size() + sizeof(float2) * screen_elems;
     if (e != cudaSuccess) {
         ts_status st = cuda_check(e, "ts_batch_create");
         free_batch(b);
         return st;
     }
     *out = reinterpret_cast<ts_batch>(b);
+    return TS_OK;
+}
+
+ts_status ts_batch_tuning(ts_batch batch, int* n_sizes, int* sizes, int* points_per_thread, int* order,
+                          int* candidates, float* us_default, float* us_chosen)
+{
+    if (!batch) return bfail(TS_ERR_INVALID_ARG, "ts_batch_tuning: null batch");
+    Batch* b = reinterpret_cast<Batch*>(batch);
+    bool present[kSizes] = {};
+    for (int i = 0; i < b->n; ++i) present[size_index(b->host_inst[i].N)] = true;
+    int k = 0;
+    for (int q = 0; q < kSizes; ++q) {
+        if (!present[q]) continue;
+        if (sizes) sizes[k] = 128 << q;
+        if (points_per_thread) points_per_thread[k] = b->e_of[q];
+        ++k;
+    }
+    if (n_sizes) *n_sizes = k;
+    if (order) *order = b->order;
+    if (candidates) *candidates = b->candidates;
+    if (us_default) *us_default = b->us_default;
+    if (us_chosen) *us_chosen = b->us_chosen;
     return TS_OK;
 }
 

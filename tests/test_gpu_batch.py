@@ -45,7 +45,7 @@ def test_batch_equals_per_instance_propagation(monkeypatch):
              (256, 20, 2e-16), (1024, 9, 5e-15)]
     seed = W.SEED_BASE + 4
     plans, fields, insts = make_instances(specs, seed)
-    batch = ts.Batch(insts, timeout_s=5.0)
+    batch = ts.Batch(insts, timeout_s=5.0, flags=ts.TS_BATCH_NO_TUNE)  # the default tile shapes
     batch.run()
     assert batch.status() == 0
     info = batch.info()
@@ -77,6 +77,36 @@ def test_batch_matches_oracle():
         phis = np.stack([O.make_screen(md, cn2, dz, 0, seed, s, i) for s in range(S)])
         ref = O.propagate(md, [dz] * S, phis, O.source_gaussian(N, 2e-3, 0.02))
         assert rel_l2(fields[i].cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("pin16", [False, True])
+def test_tuned_batch_matches_oracle_and_reports_its_choices(monkeypatch, pin16):
+    # every grid size of config 4; the autotuner's choices (or the 16-point tiles where a size has
+    # them) give the oracle's fields, and the choices are reported per N
+    if pin16:
+        monkeypatch.setenv("TS_BATCH_E", "16")
+    specs = [(256, 4, 1e-14), (512, 5, 3e-15), (1024, 4, 1e-14), (2048, 4, 1e-15)]
+    seed = 91
+    plans, fields, insts = make_instances(specs, seed)
+    batch = ts.Batch(insts)
+    batch.run()
+    assert batch.status() == 0
+    tun = batch.tuning()
+    assert set(tun["points_per_thread"]) == {256, 512, 1024, 2048}
+    assert tun["points_per_thread"][256] == 16 and tun["points_per_thread"][1024] == 32
+    if pin16:
+        assert tun["points_per_thread"][512] == 16 and tun["points_per_thread"][2048] == 16
+        assert tun["candidates"] == 0
+    else:
+        assert tun["candidates"] == 4 and 0 < tun["us_chosen"] <= tun["us_default"]
+    for i, (N, S, cn2) in enumerate(specs):
+        if N == 2048 and not pin16:
+            continue  # the oracle at N = 2048 takes long; covered by the 16-point run
+        md = O.medium(LAM, N, 2e-3, l0=5e-3, L0=10.0)
+        dz = 1000.0 / S
+        phis = np.stack([O.make_screen(md, cn2, dz, 0, seed, s, i) for s in range(S)])
+        ref = O.propagate(md, [dz] * S, phis, O.source_gaussian(N, 2e-3, 0.02))
+        assert rel_l2(fields[i].cpu().numpy(), ref) < 1e-5, (N, rel_l2(fields[i].cpu().numpy(), ref))
 
 
 def test_batch_with_given_screens_and_input_fields():
