@@ -102,9 +102,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchPara
     extern __shared__ float2 smem[];
     __shared__ int s_item;
     int last = 0;
+    int ahead = -1;  // thread 0: the item claimed one ahead of the current one (-1: none yet)
     for (;;) {
         if (threadIdx.x == 0) {
-            int it = atomicAdd(bp.head, 1);
+            // items are claimed one ahead, so no global atomic sits between two items of a CTA; a CTA
+            // always finishes its current item before it waits for the next one's dependency, and the
+            // smallest unfinished item is always some CTA's current item, so the schedule still cannot
+            // deadlock
+            int it = ahead >= 0 ? ahead : atomicAdd(bp.head, 1);
             bool stop = it >= bp.n_items || ld_relaxed(bp.err) != 0;
             if (!stop) {
                 const int4 w = bp.items[it];
@@ -129,6 +134,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchPara
                 }
             }
             s_item = stop ? -1 : it;
+            if (!stop) ahead = atomicAdd(bp.head, 1);  // its latency hides under this item
         }
         __syncthreads();
         const int it = s_item;

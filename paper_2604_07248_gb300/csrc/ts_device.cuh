@@ -349,6 +349,13 @@ struct WarpBar {
 struct BlockBar {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
+// The T threads of one line (whole consecutive warps) on named barrier `id` (1..15; 0 is the block
+// barrier): lines of a CTA exchange independently of one another.
+template <int T>
+struct LineBar {
+    int id;
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(T) : "memory"); }
+};
 
 // spectral index map f(n) = n for n < N/2, else n - N
 __device__ __forceinline__ int kidx(int n, int N) { return n < (N >> 1) ? n : n - N; }

@@ -45,7 +45,11 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
     float2* tw = smem;
     float2* buf = smem + C::tw_smem + line * RC::LS;
     float2* row = a.field + ((size_t)b * N + j) * N;
-    using Bar = typename std::conditional<(T > 32), BlockBar, WarpBar>::type;
+    // a line of more than one warp synchronises only its own warps, on its own named barrier
+    static_assert(T <= 32 || (T % 32 == 0 && kRowThreads / T <= 15), "lines of whole warps, at most 15 per CTA");
+    using Bar = typename std::conditional<(T > 32), LineBar<(T > 32 ? T : 32)>, WarpBar>::type;
+    Bar bar{};
+    if constexpr (T > 32) bar.id = 1 + line;
     if (stage_tw) stage_twiddles_c<C>(tw, a.tw);
     __syncthreads();
 
@@ -62,7 +66,7 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
 #pragma unroll
         for (int i = 0; i < E; ++i) v[i] = row[t + i * T];
     }
-    if constexpr (FLAGS & RP_IN_FREQ) line_fft_c<C, +1>(v, buf, t, tw, Bar());
+    if constexpr (FLAGS & RP_IN_FREQ) line_fft_c<C, +1>(v, buf, t, tw, bar);
     if constexpr (FLAGS & RP_PHASOR) {
         // exp(i phi) precomputed once per screen: multiply (forward) or multiply by the conjugate (adjoint)
         const float2* ph = a.phasor + (long long)((b + a.phi_off) / a.phi_group) * a.phi_set_stride + (size_t)j * N;
@@ -108,7 +112,7 @@ __device__ __forceinline__ void row_tile(const RowParams& a, int jblock, int b, 
             }
         }
     }
-    if constexpr (FLAGS & RP_OUT_FREQ) line_fft_c<C, -1>(v, buf, t, tw, Bar());
+    if constexpr (FLAGS & RP_OUT_FREQ) line_fft_c<C, -1>(v, buf, t, tw, bar);
     if constexpr (FLAGS & RP_STORE) {
 #pragma unroll
         for (int i = 0; i < E; ++i) row[t + i * T] = v[i];
