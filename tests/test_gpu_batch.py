@@ -120,6 +120,10 @@ def test_batch_with_given_screens_and_input_fields():
     fields = [torch.from_numpy(U0[b]).to(DEV) for b in range(2)]
     insts = [dict(plan=p, field=fields[b], phasor=ph[b], source=False) for b in range(2)]
     batch = ts.Batch(insts)
+    torch.cuda.synchronize()
+    # the autotuner times its candidates on scratch fields: creating the batch leaves the inputs as they were
+    for b in range(2):
+        assert np.array_equal(fields[b].cpu().numpy(), U0[b])
     batch.run()
     assert batch.status() == 0
     ref = torch.from_numpy(U0).to(DEV)

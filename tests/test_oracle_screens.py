@@ -188,7 +188,7 @@ def test_subharmonic_screens_have_the_structure_function_of_their_coefficients()
 
 
 def test_kolmogorov_structure_function_with_subharmonics():
-    # Survey pin P5 (Eq. 2-3, S18): l0 = 0, L0 = inf, N = 256, 3-level subharmonics.  (1) The oracle's
+    # Kolmogorov structure function (Eq. 2-3, S18): l0 = 0, L0 = inf, N = 256, 3-level subharmonics.  (1) The oracle's
     # screens reach the exact expectation of the discrete model at every lag.  (2) Against
     # 6.88 (r / r0)^(5/3) for 2 dx <= r <= N dx / 8 the model lies between 0.75 and 0.95: the grid
     # square itself holds >= 0.98 of D(r) (polar quadrature below), and the remaining deficit is the
