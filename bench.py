@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="CPU-baseline sample budget (and the cap on one reference-arm sample)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--overlap", action="store_true",
                     help="synthesise the next step's screens on a second stream while the current step propagates")
@@ -631,7 +632,7 @@ def run_reference(args):
     S, B = wl.S, len(wl.w0)
     cores, model = host_cpu()
     budget_total = 150.0
-    per_step_budget = min(20.0, max(2.0, budget_total / max(1, args.steps + args.warmup)))
+    per_step_budget = min(args.cpu_seconds, max(2.0, budget_total / max(1, args.steps + args.warmup)))
     for _ in range(min(args.warmup, 1)):
         oracle_rates(2.0, cores)
     rates = []
