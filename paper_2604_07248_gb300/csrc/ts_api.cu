@@ -677,16 +677,18 @@ ts_status ts_plan_create_psd(ts_plan* out, const ts_medium* medium, const ts_gri
     // separable transfer function when the dropped terms are negligible for every step:
     // dz kappa^6 / 16k^5 <= 1e-7 rad and the cross term dz kx^2 ky^2 / 4k^3 <= 0.05 rad
     {
-        bool sep = true, tiny = true;
+        bool sep = true, tiny = true, first = true;
         const double kx2 = std::pow(M_PI / grid->dx, 2.0), k = tmp.k;
         for (int s = 0; s < tmp.S; ++s) {
             const double r6 = tmp.dz[s] * kap2max * kap2max * kap2max / (16.0 * std::pow(k, 5.0));
             const double ex = tmp.dz[s] * kx2 * kx2 / (4.0 * k * k * k);
             if (r6 > 1e-7 || ex > 0.05) sep = false;
             if (ex > 0.01) tiny = false;  // exp(-i e) to second order: error e^3 / 6 <= 1.7e-7 rad
+            if (ex > 4.4e-4) first = false;  // exp(-i e) to first order: error e^2 / 2 <= 1e-7 rad
         }
         tmp.sep_transfer = sep;
         tmp.tiny_cross = sep && tiny;
+        tmp.first_order_cross = sep && tiny && first;
     }
 
     Plan* p = new Plan(tmp);

@@ -82,7 +82,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // v[i] (frequency m = t + T i of column col) *= H or conj(H), with tab(m) = (P(m), ky(m)^2, -) read
 // from the caller's shared-memory table (whatever its layout).  HMODE 0: exact angular-spectrum phase
 // beyond its paraxial part; 1: separable P' with the cross term exp(-i e) as a short series;
-// 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e.
+// 2: separable with e <= 0.01 rad, exp(-i e) = 1 - e^2/2 - i e; 3: separable with e <= 4.4e-4 rad,
+// exp(-i e) = 1 - i e (error e^2 / 2 <= 1e-7 rad, below the FP32 rounding of the product).
 template <bool CONJ, int HMODE, class Tab, int T = 32>
 __device__ __forceinline__ void transfer_tile_tab(float2 (&v)[32], Tab tab, int col, int t, float ccross,
                                                   float dcoef, float inv_k2)
@@ -113,10 +114,13 @@ __device__ __forceinline__ void transfer_tile_tab(float2 (&v)[32], Tab tab, int 
             const float e = cx * hy.z;
             const float e2 = e * e;
             h = cmul(q, make_float2(1.0f - e2 * (0.5f - e2 * (1.0f / 24.0f)), -e * (1.0f - e2 * (1.0f / 6.0f))));
-        } else {
+        } else if constexpr (HMODE == 2) {
             const float e = cx * hy.z;
             const float ce = fmaf(-0.5f * e, e, 1.0f);
             h = make_float2(fmaf(q.x, ce, q.y * e), fmaf(q.y, ce, -q.x * e));
+        } else {
+            const float e = cx * hy.z;
+            h = make_float2(fmaf(e, q.y, q.x), fmaf(-e, q.x, q.y));
         }
         v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
     }

@@ -63,6 +63,7 @@ struct Plan {
     float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)
     bool sep_transfer = false; // P includes the kappa^4 / 8k^3 term and kernels add the kx^2 ky^2 cross term
     bool tiny_cross = false;   // separable, and the cross term stays <= 0.01 rad on the whole grid
+    bool first_order_cross = false;  // tiny_cross with e <= 4.4e-4 rad: exp(-i e) = 1 - i e (error <= 1e-7 rad)
     float* dcoef = nullptr;    // [S] dz / (2 k^3)  (non-paraxial phase correction)
     float* amp = nullptr;      // [S] sqrt(2 pi k^2 dz 0.033 Cn^2) dkappa
     float* g = nullptr;        // [N][N] (kappa^2 + kappa0^2)^(-11/12) exp(-kappa^2 / 2 kappa_m^2), g(0) = 0

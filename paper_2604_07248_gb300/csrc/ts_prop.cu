@@ -77,6 +77,7 @@ cudaError_t launch_col_pass(const Plan& p, int step, bool conj, float2* field, i
     cp.err = p.d_err;
     cp.budget = p.tc_budget;
     cp.tiny_cross = p.tiny_cross;
+    cp.first_order_cross = p.first_order_cross;
     cp.stall = p.test_stall ? 1 : 0;
     cp.src_fx = p.src_fx;
     cp.src_gy = p.src_gy;

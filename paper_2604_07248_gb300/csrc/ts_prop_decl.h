@@ -36,6 +36,7 @@ struct ColParams {
     int* err;          // device error word (set when a bounded wait of a prefetching pass runs out)
     long long budget;  // clock64 cycles such a wait may take
     bool tiny_cross;   // separable form with the cross term e <= 0.01 rad: exp(-i e) to second order
+    bool first_order_cross;  // ... and e <= 4.4e-4 rad: exp(-i e) = 1 - i e (error e^2 / 2 <= 1e-7 rad)
     int stall;         // test hook: the prefetching pass skips its first copy (its first wait runs out)
     // source mode of the prefetching column pass (the first step of a call with TS_PROP_SOURCE): the
     // input R0 = FFT_rows(U0) of field b is generated in registers as the rank-one product

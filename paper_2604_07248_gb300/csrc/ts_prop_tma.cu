@@ -340,6 +340,7 @@ cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, c
         case 0: return col_launch_tma<false, 0, CT, true>(cp, B, st);
         case 1: return col_launch_tma<false, 1, CT, true>(cp, B, st);
         case 2: return col_launch_tma<false, 2, CT, true>(cp, B, st);
+        case 3: return col_launch_tma<false, 3, CT, true>(cp, B, st);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -350,6 +351,8 @@ cudaError_t col_dispatch_tma(bool conj, int hmode, const ColParams& cp, int B, c
     case 3: return col_launch_tma<true, 1, CT>(cp, B, st);
     case 4: return col_launch_tma<false, 2, CT>(cp, B, st);
     case 5: return col_launch_tma<true, 2, CT>(cp, B, st);
+    case 6: return col_launch_tma<false, 3, CT>(cp, B, st);
+    case 7: return col_launch_tma<true, 3, CT>(cp, B, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -420,9 +423,12 @@ void col_attrs(cudaError_t& e)
     chk(tma_attr(col_pass_tma_kernel<true, 1, CT>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<false, 2, CT>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<true, 2, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 3, CT>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<true, 3, CT>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<false, 0, CT, true>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<false, 1, CT, true>, CT::smem));
     chk(tma_attr(col_pass_tma_kernel<false, 2, CT, true>, CT::smem));
+    chk(tma_attr(col_pass_tma_kernel<false, 3, CT, true>, CT::smem));
 }
 template <class RT>
 void row_attrs(cudaError_t& e)
