@@ -27,6 +27,7 @@ constexpr int kBatchThreads = 256;
 struct BInst {
     int N, S, src;
     int E;  // points per thread of this instance's tiles (the batch autotuner's choice for its N)
+    int first;  // the plan bounds the transfer function's cross term by 4.4e-4 rad (first-order form)
     int tiles_row, tiles_col;
     int ctr_base;
     int extra_need;  // test hook: added to the phase-1 dependency of this instance (never satisfied)
@@ -93,6 +94,7 @@ __device__ __noinline__ void batch_col(const BInst& I, int phase, int tile, floa
     c.tw = I.tw;
     c.P = I.P + (size_t)s * N;
     c.ccross = I.ccross[s];
+    c.first_order_cross = I.first != 0;
     c.dk = I.dk;
     col_tile<N, E, false, true>(c, tile, 0, smem, stage);
 }
@@ -501,6 +503,7 @@ ts_status ts_batch_create(ts_batch* out, const ts_batch_instance* inst, int n, d
         ctr += 2 * p->S + 1;
         bi.extra_need = ((flags & TS_BATCH_TEST_STALL) && i == 0) ? 1 : 0;
         bi.src_coef = p->src_coef[0];
+        bi.first = p->first_order_cross ? 1 : 0;
         bi.dk = (float)p->dk;
         bi.field = reinterpret_cast<float2*>(inst[i].field);
         bi.P = p->P;

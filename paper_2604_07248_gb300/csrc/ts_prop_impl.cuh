@@ -251,12 +251,24 @@ __device__ __forceinline__ void apply_transfer(float2 (&v)[E], const ColParams& 
     const float2 px = Ps[col];
     if constexpr (SEP) {
         const float cx = a.ccross * kx * kx;
+        if (a.first_order_cross) {  // e <= 4.4e-4 rad on the whole grid: exp(-i e) = 1 - i e
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + i * T;
-            const float ky = a.dk * (float)kidx(m, N);
-            const float2 h = cmul(cmul(px, Ps[m]), small_phase(cx * ky * ky));
-            v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+            for (int i = 0; i < E; ++i) {
+                const int m = t + i * T;
+                const float ky = a.dk * (float)kidx(m, N);
+                const float2 q = cmul(px, Ps[m]);
+                const float e = cx * ky * ky;
+                const float2 h = make_float2(fmaf(e, q.y, q.x), fmaf(-e, q.x, q.y));
+                v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + i * T;
+                const float ky = a.dk * (float)kidx(m, N);
+                const float2 h = cmul(cmul(px, Ps[m]), small_phase(cx * ky * ky));
+                v[i] = CONJ ? cmulc(v[i], h) : cmul(v[i], h);
+            }
         }
     } else {
 #pragma unroll
