@@ -420,7 +420,8 @@ typedef struct {
  * columns of a column tile: N = 512 and 2048 at 32 or 16, N = 1024 at 32, N <= 256 at 16 -- and the
  * order of instances within a phase (as given, or largest grids first), by timing whole replays of
  * the batch on scratch fields it allocates for the purpose and frees (the callers' fields are not
- * touched); ts_batch_tuning reports the choices.  The call synchronises the device.
+ * touched; without room for them the batch keeps the default configuration, untuned);
+ * ts_batch_tuning reports the choices.  The call synchronises the device.
  * Copies `inst`; the plans, fields and screens must outlive the batch. */
 ts_status ts_batch_create(ts_batch* batch, const ts_batch_instance* inst, int n, double timeout_s, int flags);
 

@@ -405,13 +405,29 @@ cudaError_t time_installed(Batch& b, int rounds, float* us)
 cudaError_t autotune_batch(Batch& b, std::vector<int4>& items)
 {
     std::vector<float2*> scratch(b.n, nullptr), real(b.n);
+    for (int i = 0; i < b.n; ++i) real[i] = b.host_inst[i].field;
+    auto release = [&]() {
+        for (int i = 0; i < b.n; ++i) {
+            b.host_inst[i].field = real[i];
+            if (scratch[i]) cudaFree(scratch[i]);
+            scratch[i] = nullptr;
+        }
+    };
+    for (int i = 0; i < b.n; ++i) {
+        const size_t n2 = (size_t)b.host_inst[i].N * b.host_inst[i].N;
+        if (cudaMalloc(&scratch[i], sizeof(float2) * n2) != cudaSuccess) {
+            // no room for the scratch fields: keep the default configuration, untuned
+            (void)cudaGetLastError();
+            scratch[i] = nullptr;
+            release();
+            b.candidates = 0;
+            return cudaSuccess;
+        }
+    }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < b.n && e == cudaSuccess; ++i) {
-        real[i] = b.host_inst[i].field;
-        const size_t n2 = (size_t)b.host_inst[i].N * b.host_inst[i].N;
-        e = cudaMalloc(&scratch[i], sizeof(float2) * n2);
-        if (e == cudaSuccess) e = cudaMemset(scratch[i], 0, sizeof(float2) * n2);
-        if (e == cudaSuccess) b.host_inst[i].field = scratch[i];
+        e = cudaMemset(scratch[i], 0, sizeof(float2) * (size_t)b.host_inst[i].N * b.host_inst[i].N);
+        b.host_inst[i].field = scratch[i];
     }
     auto measure = [&](float* us) -> cudaError_t {
         lay_out(b, items);
@@ -446,10 +462,7 @@ cudaError_t autotune_batch(Batch& b, std::vector<int4>& items)
     }
     b.us_chosen = best;
     if (e == cudaSuccess) e = cudaStreamSynchronize(b.cap);
-    for (int i = 0; i < b.n; ++i) {
-        b.host_inst[i].field = real[i];
-        if (scratch[i]) cudaFree(scratch[i]);
-    }
+    release();
     return e;
 }
 
