@@ -1,6 +1,6 @@
 // ts_async.cuh -- asynchronous-copy building blocks of the persistent N = 1024 passes (sm_103a):
-// mbarriers with bounded waits, TMA tensor and bulk copies global -> shared, proxy fences, acquire
-// loads, and the transfer-function multiply of a column tile (Eq. 1, angular-spectrum H).
+// mbarriers with bounded waits, TMA tensor and bulk copies global -> shared, TMA tensor stores
+// shared -> global with bulk-group waits, proxy fences, acquire loads, and the transfer-function multiply of a column tile (Eq. 1, angular-spectrum H).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -71,6 +71,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(s32(m))
         : "memory");
 }
+// 2-D tiled tensor copy shared -> global, completion tracked by this thread's bulk groups
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(s32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+// closes this thread's bulk stores issued since the last commit into one bulk group
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// waits until at most PENDING of this thread's most recent bulk groups still read shared memory
+template <int PENDING = 0>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(PENDING) : "memory");
+}
+// waits until every bulk group of this thread has completed (its global writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // contiguous bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m)
 {

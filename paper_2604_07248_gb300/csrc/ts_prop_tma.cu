@@ -4,10 +4,13 @@
 // line.
 //
 // Column pass: a CTA of T W threads owns W-column tiles of 64 KiB (N = 1024: W = 8, or W = 4 with
-// 32 KiB tiles; N = 512: W = 16).  Tile k+1 is loaded by 2-D tensor copies (boxes of 256 rows x 2W
-// floats) into the CTA's exchange buffer as soon as the last exchange of tile k has been read, so the
-// load runs under the last FFT stage and the stores of tile k.  Thread (t, c) = (tid / W, tid % W)
-// holds points t + T i of column c.
+// 32 KiB tiles; N = 512: W = 16).  The tile comes in by 2-D tensor copies (boxes of 256 rows x 2W
+// floats) into the CTA's exchange buffer and goes out the same way: after the last FFT stage the
+// threads write tile k into the buffer in its global layout, one thread issues the tensor stores of
+// its boxes, and box q of tile k+1 is loaded into the buffer as soon as the store of box q has read
+// it.  The stores leave the threads at once (no per-thread global stores to drain); the load of the
+// next tile is covered by the other CTA on the SM.  Thread (t, c) = (tid / W, tid % W) holds points
+// t + T i of column c.
 //
 // Row pass: every warp owns 32 / T consecutive rows at a time (one at N = 1024, two at 512) and its
 // own 8 KiB of line buffers, with its own mbarrier: the phasor rows of the step are bulk-copied into
@@ -124,6 +127,8 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
         const int b = tile / TPF, col = (tile % TPF) * W + c;
         float2 v[32];
         if constexpr (SRC) {
+            // the previous tile's bulk store has read the buffer (thread 0 waited) before it is reused
+            __syncthreads();
             // the source's row transform: a rank-one product, no input to load
             const int s = (b + a.src_off) % a.n_src;
             const float2 fx = __ldg(a.src_fx + (size_t)s * N + col);
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
             }
             if (__syncthreads_or(!ok)) {  // every thread has read the tile before the exchange reuses it
                 if (tid == 0) {
+                    bulk_wait_all();
                     atomicExch(a.err, kErrTmaWait);
                     mbar_wait(bar, parity, a.budget);  // the copy in flight, bounded again
                 }
@@ -168,15 +174,48 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
             stage0_exchange_x4<+1>(v, line, t, BlockBar());
         else
             fft_stage_c<C, 0, +1>(v, line, t, tw, BlockBar());
-        if (!SRC && tid == 0 && tile + (int)gridDim.x < tiles) {
-            fence_proxy_async();
-            issue(tile + gridDim.x);
-        }
         fft_stage_c<C, 1, +1>(v, line, t, tw, BlockBar());
-        float2* base = a.field + (size_t)b * N * N + col;
+        // the tile goes out through the buffer by tensor stores; the next tile comes in once they
+        // have read it
 #pragma unroll
-        for (int i = 0; i < 32; ++i) base[(size_t)(t + T * i) * N] = v[i];
+        for (int i = 0; i < 32; ++i) buf[(t + T * i) * W + c] = v[i];
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            constexpr int Q = N / CT::BOX_ROWS;
+            static_assert(Q == 4 || Q == 2, "quarter or half boxes");
+            const int x = 2 * (tile % TPF) * W;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {  // one bulk group per box
+                tma_store_2d(&tmap, buf + q * CT::BOX_ROWS * W, x, b * N + q * CT::BOX_ROWS);
+                bulk_commit();
+            }
+            if (!SRC && tile + (int)gridDim.x < tiles) {
+                // box q of the next tile comes in as soon as the store of box q has read it
+                const int tn = tile + gridDim.x, bn = tn / TPF, xn = 2 * (tn % TPF) * W;
+                mbar_expect_tx(bar, CT::TILE_BYTES);
+                auto load_box = [&](int q) { tma_load_2d(buf + q * CT::BOX_ROWS * W, &tmap, xn, bn * N + q * CT::BOX_ROWS, bar); };
+                if constexpr (Q == 4) {
+                    bulk_wait_read<3>();
+                    load_box(0);
+                    bulk_wait_read<2>();
+                    load_box(1);
+                    bulk_wait_read<1>();
+                    load_box(2);
+                    bulk_wait_read<0>();
+                    load_box(3);
+                } else {
+                    bulk_wait_read<1>();
+                    load_box(0);
+                    bulk_wait_read<0>();
+                    load_box(1);
+                }
+            } else {
+                bulk_wait_read<0>();
+            }
+        }
     }
+    if (tid == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------------------------
