@@ -147,7 +147,10 @@ __device__ __forceinline__ float2 twiddle_const(float2 v)
 // is a compile-time constant after unrolling, so x stays in registers.  In the butterflies, a twiddle
 // of +-i becomes scalar adds with the sign folded in, and one of the odd multiples of pi/4 becomes
 // t = (+-o.x -+ o.y, ...) followed by e +- t / sqrt(2) as packed FMAs (2 instructions saved each).
-template <int R, int SIGN>
+// Any other twiddle W: with FB, x[K] = e + W o as four FMAs (the product fused into the add) and
+// x[K + R/2] = 2 e - x[K] as two, 6 FMA-pipe cycles per butterfly; without FB, W o (4) then a
+// packed add and subtract (2 cycles each), 8 cycles.  The two differ only in rounding.
+template <int R, int SIGN, bool FB = true>
 struct Dft {
     __device__ __forceinline__ static void run(float2* x)
     {
@@ -157,8 +160,8 @@ struct Dft {
             e[n] = x[2 * n];
             o[n] = x[2 * n + 1];
         }
-        Dft<R / 2, SIGN>::run(e);
-        Dft<R / 2, SIGN>::run(o);
+        Dft<R / 2, SIGN, FB>::run(e);
+        Dft<R / 2, SIGN, FB>::run(o);
         combine<0>(x, e, o);
     }
     template <int K>
@@ -179,18 +182,25 @@ struct Dft {
                 const float2 t = make_float2(sr * o[K].x - si * o[K].y, sr * o[K].y + si * o[K].x);
                 x[K] = __ffma2_rn(make_float2(c, c), t, e[K]);
                 x[K + R / 2] = __ffma2_rn(make_float2(-c, -c), t, e[K]);
-            } else {
+            } else if constexpr (k32 == 0 || !FB) {
                 const float2 t = twiddle_const<R, K, SIGN>(o[K]);
                 x[K] = cadd(e[K], t);
                 x[K + R / 2] = csub(e[K], t);
+            } else {
+                constexpr float c = (float)cos32(k32);
+                constexpr float s = (float)(SIGN * sin32(k32));
+                const float re = fmaf(c, o[K].x, fmaf(-s, o[K].y, e[K].x));
+                const float im = fmaf(c, o[K].y, fmaf(s, o[K].x, e[K].y));
+                x[K] = make_float2(re, im);
+                x[K + R / 2] = make_float2(fmaf(2.0f, e[K].x, -re), fmaf(2.0f, e[K].y, -im));
             }
             combine<K + 1>(x, e, o);
         }
     }
 };
 
-template <int SIGN>
-struct Dft<2, SIGN> {
+template <int SIGN, bool FB>
+struct Dft<2, SIGN, FB> {
     __device__ __forceinline__ static void run(float2* x)
     {
         const float2 a = x[0], b = x[1];
@@ -199,19 +209,19 @@ struct Dft<2, SIGN> {
     }
 };
 
-template <int SIGN>
-struct Dft<1, SIGN> {
+template <int SIGN, bool FB>
+struct Dft<1, SIGN, FB> {
     __device__ __forceinline__ static void run(float2*) {}
 };
 
 // Strided wrapper: transforms v[0], v[S], ..., v[(R-1) S].
-template <int R, int SIGN, int S>
+template <int R, int SIGN, int S, bool FB = true>
 __device__ __forceinline__ void dft_strided(float2* v)
 {
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = v[r * S];
-    Dft<R, SIGN>::run(x);
+    Dft<R, SIGN, FB>::run(x);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r * S] = x[r];
 }
@@ -219,10 +229,12 @@ __device__ __forceinline__ void dft_strided(float2* v)
 // ----------------------------------------------------------------------------------------------
 // Stockham line FFT configuration.  E points per thread (default 16 for N <= 256, else 32; a kernel
 // may choose another power of two), T = N / E threads per line.  Stage k has sub-length
-// Ns_k = E^k and radix R_k = min(E, N / Ns_k).
+// Ns_k = E^k and radix R_k = min(E, N / Ns_k).  FB selects the butterfly form of the in-register
+// DFTs (see Dft).
 // ----------------------------------------------------------------------------------------------
-template <int N, int EE = 0>
+template <int N, int EE = 0, bool FB = true>
 struct FftCfg {
+    static constexpr bool fused_butterflies = FB;
     static constexpr int E = EE ? EE : ((N <= 256) ? 16 : 32);
     static constexpr int T = N / E;
     static constexpr int stages = (N <= E) ? 1 : (N <= E * E ? 2 : 3);
@@ -284,7 +296,7 @@ __device__ __forceinline__ void fft_stage_m(float2 (&v)[C::E], Map map, int t, c
             }
             }
         }
-        dft_strided<R, SIGN, B>(v + q);
+        dft_strided<R, SIGN, B, C::fused_butterflies>(v + q);
     }
     if constexpr (!LAST) {
 #pragma unroll

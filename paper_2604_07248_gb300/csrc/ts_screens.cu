@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(SColCfg<N>::THREADS) screen_col_kernel(const S
         for (int i = 0; i < E; ++i) sp[(size_t)(t + i * T) * N] = v[i];
     }
     __syncthreads();
-    line_fft<N, +1>(v, buf, t, tw, BlockBar());
+    // the synthesis keeps the packed-add butterflies: the fused form measured slower here
+    line_fft_c<FftCfg<N, 0, false>, +1>(v, buf, t, tw, BlockBar());
     float2* yo = a.y + (size_t)z * N * N + n;
 #pragma unroll
     for (int i = 0; i < E; ++i) yo[(size_t)(t + i * T) * N] = v[i];
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(SRowCfg<N>::THREADS) screen_row_kernel(const S
     for (int i = 0; i < E; ++i) v[i] = yrow[t + i * T];
     stage_twiddles<N>(tw, a.tw);
     __syncthreads();
-    line_fft<N, +1>(v, buf, t, tw, Bar());
+    line_fft_c<FftCfg<N, 0, false>, +1>(v, buf, t, tw, Bar());
     const size_t roff = ((size_t)z * N + j) * N;
     // phi in v[i].x, then stored as requested: float32 screen and/or its phasor exp(i phi)
     if constexpr (SH) {
