@@ -233,11 +233,13 @@ __device__ __forceinline__ void dft_strided(float2* v)
 // Stockham line FFT configuration.  E points per thread (default 16 for N <= 256, else 32; a kernel
 // may choose another power of two), T = N / E threads per line.  Stage k has sub-length
 // Ns_k = E^k and radix R_k = min(E, N / Ns_k).  FB selects the butterfly form of the in-register
-// DFTs (see Dft).
+// DFTs (see Dft); TF folds the twiddles of radix-32 stages into the DFT's first butterfly level
+// (see fft_stage_m; the persistent N = 1024 passes use it, the per-CTA tiles measured faster without).
 // ----------------------------------------------------------------------------------------------
-template <int N, int EE = 0, bool FB = true>
+template <int N, int EE = 0, bool FB = true, bool TF = false>
 struct FftCfg {
     static constexpr bool fused_butterflies = FB;
+    static constexpr bool fold_twiddles = FB && TF;
     static constexpr int E = EE ? EE : ((N <= 256) ? 16 : 32);
     static constexpr int T = N / E;
     static constexpr int stages = (N <= E) ? 1 : (N <= E * E ? 2 : 3);
@@ -285,7 +287,7 @@ __device__ __forceinline__ void fft_stage_m(float2 (&v)[C::E], Map map, int t, c
             if constexpr (R == 2) {
                 const float2 wa = tw[C::tw_off(K) + jm];
                 v[q + B] = SIGN < 0 ? cmul(v[q + B], wa) : cmulc(v[q + B], wa);
-            } else if constexpr (C::fused_butterflies && R == 32) {
+            } else if constexpr (C::fold_twiddles && R == 32) {
                 // the stage twiddles fused into the DFT's first butterfly level: for each pair
                 // (r, r + R/2), a = w_r v_r, then v_r = a + w v, v_(r+R/2) = 2 a - v_r (10 FMA-pipe
                 // cycles per pair instead of 12; at radix 16 the separate multiplies measured faster)

@@ -61,7 +61,7 @@ __device__ __forceinline__ void stage0_exchange_x4(float2 (&v)[32], float2* line
 template <int N_, int W_>
 struct ColTma {
     static constexpr int N = N_, W = W_;
-    using C = FftCfg<N, 32>;  // T = N / 32 threads per column, 32 points each
+    using C = FftCfg<N, 32, true, true>;  // T = N / 32 threads per column, 32 points each
     static constexpr int T = C::T, THREADS = T * W, PER_SM = 512 / THREADS, BOX_ROWS = 256;
     static constexpr bool SPLIT = PER_SM > 2;
     static constexpr int TPF = N / W;                        // tiles per field
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(CT::THREADS, CT::PER_SM)
 template <int N_>
 struct RowTma {
     static constexpr int N = N_;
-    using C = FftCfg<N, 32>;  // T = N / 32 threads per row, 32 / T rows per warp
+    using C = FftCfg<N, 32, true, true>;  // T = N / 32 threads per row, 32 / T rows per warp
     static constexpr int T = C::T, RPW = 32 / T;
     static constexpr int WARPS = 8, THREADS = 32 * WARPS;
     // line stride (float2); a line holds the dense row or the exchange (N = 1024: the 16-byte exchange)
