@@ -179,10 +179,10 @@ def screen_bytes(N, n_screens, ar=False):
     return N * N * (n_screens * ((16 if ar else 0) + 16 + 8) + 4)
 
 
-def load_traffic(kind_name):
+def load_traffic(kind_name, variant=None):
     """(cold-cache DRAM bytes per launch, median warm-cache bytes per 4-field launch) of a kernel from
     the committed ncu summary, or (None, None) when any source file the kernel is built from changed
-    since the counters were taken."""
+    since the counters were taken, or when the record is of another kernel variant than `variant`."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None, None
@@ -192,6 +192,8 @@ def load_traffic(kind_name):
         return None, None
     from paper_2604_07248_gb300 import _build
     if k is None or k.get("sources_sha") != _build.files_sha(k.get("sources", [])):
+        return None, None
+    if variant is not None and k.get("variant") is not None and k.get("variant") != variant:
         return None, None
     warm = k.get("warm_dram_bytes_per_launch_4_fields")
     return k.get("dram_bytes_per_launch"), (int(statistics.median(warm)) if warm else None)
@@ -336,7 +338,8 @@ def run_gpu(args):
             per_kernel[name]["share"] = round(kt[k][1] / total, 4) if total > 0 else None
     dom = max(per_kernel, key=lambda n: per_kernel[n]["share"] or 0)
     dk = per_kernel[dom]
-    traffic, traffic_warm = load_traffic(dom)
+    # the record holds one column and one row variant: the one the autotuner picks at this workload
+    traffic, traffic_warm = load_traffic(dom, {"col_pass": tune[5], "row_pass": tune[7]}.get(dom))
     roof = {"bound": "hbm", "kernel": dom, "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": round(dk["achieved_gbs"] / peak, 4), "traffic": traffic,
             "traffic_note": "ncu dram read + write per 8-field launch, cold caches (ncu flushes before replay), from the "
