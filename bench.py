@@ -494,6 +494,9 @@ def run_gpu(args):
                                         [round(x, 2) if isinstance(x, float) else
                                          ([round(y, 2) for y in x] if isinstance(x, list) else x)
                                          for x in plan.tuning()])),
+                   "column_tiles": dict(zip(("col_variant", "us_8_columns_grouped", "us_4_columns_grouped"),
+                                            [round(x, 2) if isinstance(x, float) else x
+                                             for x in plan.tuning_columns()])),
                    "fused": {"chosen": fused[0], "us_per_pass": round(fused[1], 2), "us_fused": round(fused[2], 2)},
                    "l2": "working set 320 MiB (AR spectra 128 + screen phasors 128 + fields 64) > 126 MB L2; no flush"},
         "roofline": roof,

@@ -168,6 +168,17 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
 ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
                                     int* row_variant, float* us);
 
+/* The column tiles under concurrent field groups (N = 1024, 32 points per thread, FP32 passes): when
+ * the autotuner propagates two or more field groups concurrently and its first stage picked a
+ * prefetching column pass (8- or 4-column tiles, column variant 2 or 3), it times both again as runs
+ * of column + row pass pairs on that many groups and keeps the faster (the other replaces the first
+ * stage's pick only when at least 1 % faster).  *col_variant receives the column variant ts_propagate
+ * uses; us_8_columns / us_4_columns the two costs in microseconds per pass pair (0 = not timed: fewer
+ * than two groups, another variant, other N, or TS_COL_VARIANT / TS_PROP_STREAMS in the environment; a
+ * choice cached from an earlier plan reports the timings it was made on).  Outputs other than
+ * col_variant may be NULL.  Host-only. */
+ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_8_columns, float* us_4_columns);
+
 /* The autotuner's last stage (N = 1024, 32 points per thread, FP32 passes): *fused = 1 when
  * ts_propagate runs the whole path of a call -- first row pass and S x (column pass, row pass) of
  * Eq. 1 -- as ONE persistent launch.  Its work items are (pass, field, 8-column or 8-row tile); an

@@ -71,6 +71,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "ts_plan_tuning_candidates": (_I, [_P, _I, C.POINTER(C.c_int), _P, _P, _P, _P]),
     "ts_plan_tuning_fused": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "ts_plan_tuning_columns": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "ts_max_step": (_D, [C.POINTER(Medium), C.POINTER(Grid)]),
     "ts_cn2_hufnagel_valley": (_I, [_P, _I, _D, _D, _P]),
     "ts_adam_step": (_I, [_P, _P, _P, _P, C.c_longlong, _D, _D, _D, _D, _I, _P]),
@@ -359,6 +360,13 @@ class Plan:
         _check(load().ts_plan_tuning_candidates(self._h, n.value, C.byref(n), e, cv, rv, us),
                "ts_plan_tuning_candidates")
         return [(e[i], cv[i], rv[i], us[i]) for i in range(n.value)]
+
+    def tuning_columns(self):
+        """(column variant in use, us per pass pair with 8-column tiles, with 4-column tiles), the last
+        two timed under the chosen concurrent field groups (0 when not timed)."""
+        v, a, b = C.c_int(), C.c_float(), C.c_float()
+        _check(load().ts_plan_tuning_columns(self._h, C.byref(v), C.byref(a), C.byref(b)), "ts_plan_tuning_columns")
+        return v.value, a.value, b.value
 
     def tuning_fused(self):
         """(fused, us per propagation with per-pass launches, us with the fused persistent launch)."""

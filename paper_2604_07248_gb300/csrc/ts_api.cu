@@ -416,9 +416,19 @@ ts_status autotune(Plan& p)
 
 // Second autotuner stage: how many field groups to propagate concurrently (1, 2 or 4 streams), timed
 // as runs of four column + row pass pairs of B_t workspace fields per fork (the reported cost is per
-// pair).  Cached like the first stage;
-// TS_PROP_STREAMS=1|2|4 forces a choice.
-std::map<std::tuple<int, int, int, int, int>, int> g_group_cache;
+// pair).  Then, when that is two or more groups at N = 1024 with a prefetching column variant (8- or
+// 4-column tiles), both column variants are timed again the same way with that many groups: on one
+// stream the two come within a few per cent of each other (so the first stage's pick between them
+// follows noise), while under concurrent groups they differ, so the column variant is taken from
+// this timing (the other one replaces the first stage's pick only when at least 1 % faster).  Cached
+// like the first stage; TS_PROP_STREAMS=1|2|4 forces the group count and skips both timings,
+// TS_COL_VARIANT skips the second.
+struct GroupChoice {
+    int groups;
+    int col_variant;  // -1: the first stage's pick stands
+    float us_cols[2];  // cost per pass pair of 8- / 4-column tiles with `groups` groups (0: not timed)
+};
+std::map<std::tuple<int, int, int, int, int>, GroupChoice> g_group_cache;
 constexpr int kTuneSteps = 4;  // column + row pass pairs per fork in the group timing
 
 ts_status autotune_groups(Plan& p)
@@ -439,7 +449,10 @@ ts_status autotune_groups(Plan& p)
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_group_cache.find(key);
         if (it != g_group_cache.end()) {
-            p.prop_groups = it->second;
+            p.prop_groups = it->second.groups;
+            if (it->second.col_variant >= 0) p.col_variant = it->second.col_variant;
+            p.tune_col_us[0] = it->second.us_cols[0];  // the timings the cached choice was made on
+            p.tune_col_us[1] = it->second.us_cols[1];
             return TS_OK;
         }
     }
@@ -451,10 +464,8 @@ ts_status autotune_groups(Plan& p)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int cand[3] = {1, 2, 4};
     float t_min[3] = {1e30f, 1e30f, 1e30f};
-    for (int rd = 0; rd < kTuneRounds * 3 && e == cudaSuccess; ++rd) {  // interleaved rounds, as above
-        const int c = rd % 3;
-        const int groups = cand[c];
-        if (groups > Bt) continue;
+    // microseconds per column + row pass pair of `groups` concurrent groups (2 warm-up + 5 timed runs)
+    auto time_groups = [&](int groups, float& us) {
         auto once = [&]() {
             cudaError_t x = cudaEventRecord(p.fork, nullptr);
             for (int g = 1; g < groups && x == cudaSuccess; ++g) x = cudaStreamWaitEvent(p.aux[g - 1], p.fork, 0);
@@ -489,14 +500,15 @@ ts_status autotune_groups(Plan& p)
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess) t_min[c] = std::min(t_min[c], ms * 1000.0f / (5.0f * kTuneSteps));
+        if (e == cudaSuccess) us = std::min(us, ms * 1000.0f / (5.0f * kTuneSteps));
+    };
+    for (int rd = 0; rd < kTuneRounds * 3 && e == cudaSuccess; ++rd) {  // interleaved rounds, as above
+        const int c = rd % 3;
+        if (cand[c] <= Bt) time_groups(cand[c], t_min[c]);
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (groups)");
     float best = 1e30f;
     int best_g = 1;
-    for (int c = 0; c < 3 && cand[c] <= Bt; ++c) {
+    for (int c = 0; c < 3 && cand[c] <= Bt && e == cudaSuccess; ++c) {
         p.tune_group_us[c] = t_min[c];
         if (t_min[c] < best * 0.97f) {  // prefer fewer streams unless 3 % faster
             best = t_min[c];
@@ -504,8 +516,28 @@ ts_status autotune_groups(Plan& p)
         }
     }
     p.prop_groups = best_g;
+    // the column tiles under the chosen concurrency
+    GroupChoice gc{best_g, -1, {0.0f, 0.0f}};
+    const bool retime = e == cudaSuccess && best_g >= 2 && p.N == 1024 && p.fft_e == 32 && !p.split_bf16 &&
+                        (p.col_variant == 2 || p.col_variant == 3) && std::getenv("TS_COL_VARIANT") == nullptr;
+    if (retime) {
+        const int first = p.col_variant;
+        float us[2] = {1e30f, 1e30f};
+        for (int rd = 0; rd < kTuneRounds * 2 && e == cudaSuccess; ++rd) {
+            p.col_variant = 2 + rd % 2;
+            time_groups(best_g, us[rd % 2]);
+        }
+        const int other = first == 2 ? 3 : 2;
+        p.col_variant = (e == cudaSuccess && us[other - 2] < 0.99f * us[first - 2]) ? other : first;
+        if (e == cudaSuccess) gc = GroupChoice{best_g, p.col_variant, {us[0], us[1]}};
+        p.tune_col_us[0] = gc.us_cols[0];
+        p.tune_col_us[1] = gc.us_cols[1];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(e, "ts_plan_create autotune (groups)");
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_group_cache[key] = best_g;
+    g_group_cache[key] = gc;
     return TS_OK;
 }
 
@@ -847,6 +879,16 @@ ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_p
         if (row_variant) row_variant[c] = kCandRow[c];
         if (us) us[c] = p->tune_us[c];
     }
+    return TS_OK;
+}
+
+ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_8_columns, float* us_4_columns)
+{
+    if (!plan || !col_variant) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning_columns: need plan and output");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    *col_variant = p->col_variant;
+    if (us_8_columns) *us_8_columns = p->tune_col_us[0];
+    if (us_4_columns) *us_4_columns = p->tune_col_us[1];
     return TS_OK;
 }
 

@@ -58,6 +58,7 @@ struct Plan {
     float4* ht_all = nullptr;  // [S][N] (P_s, ky^2) for the fused launch (N = 1024)
     int* fused_ctr = nullptr;  // [(2S+1) max_batch + 1] completion counters and work counter of the fused launch
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
+    float tune_col_us[2] = {0, 0};       // 8- / 4-column tiles re-timed under the chosen field groups (0: not)
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)

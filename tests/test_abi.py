@@ -143,6 +143,7 @@ def test_every_plan_entry_point_refuses_a_null_handle_without_a_gpu():
         "ts_plan_tuning": (N,) + (None,) * 9,
         "ts_plan_tuning_candidates": (N, 0, None, None, None, None, None),
         "ts_plan_tuning_fused": (N, None, None, None),
+        "ts_plan_tuning_columns": (N, None, None, None),
         "ts_plan_set_sources": (N, 1, None),
         "ts_make_sources": (N, None, 1, None),
         "ts_make_screens": (N, 1, 0, 1, None, None, None),
