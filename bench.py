@@ -494,7 +494,7 @@ def run_gpu(args):
                                         [round(x, 2) if isinstance(x, float) else
                                          ([round(y, 2) for y in x] if isinstance(x, list) else x)
                                          for x in plan.tuning()])),
-                   "column_tiles": dict(zip(("col_variant", "us_8_columns_grouped", "us_4_columns_grouped"),
+                   "column_tiles": dict(zip(("col_variant", "us_variant2_grouped", "us_variant3_grouped"),
                                             [round(x, 2) if isinstance(x, float) else x
                                              for x in plan.tuning_columns()])),
                    "fused": {"chosen": fused[0], "us_per_pass": round(fused[1], 2), "us_fused": round(fused[2], 2)},

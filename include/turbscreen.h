@@ -157,27 +157,27 @@ ts_status ts_plan_tuning(ts_plan plan, int* points_per_thread, float* us_e16, fl
 
 /* The autotuner's whole candidate table: *n receives the number of candidates (8); for the first
  * min(max, *n) of them, points_per_thread[c] (16 or 32), col_variant[c] (0: a column line shared by
- * four warps; 1: one warp per column, tile staged through shared memory; 2 / 3: persistent CTAs (two /
- * four per SM) whose next 8- / 4-column tile arrives by TMA while the current one is transformed),
- * row_variant[c] (0: each CTA
+ * four warps; 1: one warp per column, tile staged through shared memory; 2 / 3: persistent CTAs whose
+ * next tile arrives by TMA while the current one is transformed, wide / narrow tiles: 8 / 4 columns
+ * (two / four CTAs per SM) at N = 1024, 16 / 8 columns at N = 512), row_variant[c] (0: each CTA
  * reads its screen rows; 1: phasor rows shared by the CTA's fields; 2: persistent warps that prefetch
  * their next field row and the screen phasor row with bulk asynchronous copies) and us[c], the timed
- * cost in microseconds of one column + one row pass (0 = not timed).  Variants 2 exist for N = 512
- * and 1024, variants 1 and 3 for
- * N = 1024 at 32 points per thread.  Output arrays may be NULL.  Host-only; no device work. */
+ * cost in microseconds of one column + one row pass (0 = not timed).  Column variants 2 and 3 and row
+ * variant 2 exist for N = 512 and 1024, column variant 1 and row variant 1 for N = 1024, all at 32
+ * points per thread.  Output arrays may be NULL.  Host-only; no device work. */
 ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_per_thread, int* col_variant,
                                     int* row_variant, float* us);
 
-/* The column tiles under concurrent field groups (N = 1024, 32 points per thread, FP32 passes): when
- * the autotuner propagates two or more field groups concurrently and its first stage picked a
- * prefetching column pass (8- or 4-column tiles, column variant 2 or 3), it times both again as runs
- * of column + row pass pairs on that many groups and keeps the faster (the other replaces the first
- * stage's pick only when at least 1 % faster).  *col_variant receives the column variant ts_propagate
- * uses; us_8_columns / us_4_columns the two costs in microseconds per pass pair (0 = not timed: fewer
- * than two groups, another variant, other N, or TS_COL_VARIANT / TS_PROP_STREAMS in the environment; a
- * choice cached from an earlier plan reports the timings it was made on).  Outputs other than
- * col_variant may be NULL.  Host-only. */
-ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_8_columns, float* us_4_columns);
+/* The column tiles under concurrent field groups (N = 512 and 1024, 32 points per thread, FP32
+ * passes): when the autotuner propagates two or more field groups concurrently and its first stage
+ * picked a prefetching column pass (column variant 2 or 3: wide or narrow tiles), it times both again
+ * as runs of column + row pass pairs on that many groups and keeps the faster (the other replaces the
+ * first stage's pick only when at least 1 % faster).  *col_variant receives the column variant
+ * ts_propagate uses; us_variant2 / us_variant3 the two costs in microseconds per pass pair (0 = not
+ * timed: fewer than two groups, another variant, other N, or TS_COL_VARIANT / TS_PROP_STREAMS in the
+ * environment; a choice cached from an earlier plan reports the timings it was made on).  Outputs
+ * other than col_variant may be NULL.  Host-only. */
+ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_variant2, float* us_variant3);
 
 /* The autotuner's last stage (N = 1024, 32 points per thread, FP32 passes): *fused = 1 when
  * ts_propagate runs the whole path of a call -- first row pass and S x (column pass, row pass) of

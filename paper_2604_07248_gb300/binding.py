@@ -362,8 +362,8 @@ class Plan:
         return [(e[i], cv[i], rv[i], us[i]) for i in range(n.value)]
 
     def tuning_columns(self):
-        """(column variant in use, us per pass pair with 8-column tiles, with 4-column tiles), the last
-        two timed under the chosen concurrent field groups (0 when not timed)."""
+        """(column variant in use, us per pass pair with column variant 2 (wide tiles), with variant 3
+        (narrow tiles)), the last two timed under the chosen concurrent field groups (0 when not timed)."""
         v, a, b = C.c_int(), C.c_float(), C.c_float()
         _check(load().ts_plan_tuning_columns(self._h, C.byref(v), C.byref(a), C.byref(b)), "ts_plan_tuning_columns")
         return v.value, a.value, b.value

@@ -322,9 +322,9 @@ ts_status autotune(Plan& p)
     bool use[kCand];
     int n_use = 0, only = -1;
     for (int c = 0; c < kCand; ++c) {
-        // column variants 1 and 3 and row variant 1 exist for N = 1024, the prefetching variants 2
-        // for N = 512 and 1024
-        const bool avail_v = cand_v[c] == 0 || p.N == 1024 || (cand_v[c] == 2 && p.N == 512);
+        // column variant 1 and row variant 1 exist for N = 1024, the prefetching column variants 2 and 3
+        // (wide and narrow tiles) and row variant 2 for N = 512 and 1024
+        const bool avail_v = cand_v[c] == 0 || p.N == 1024 || ((cand_v[c] == 2 || cand_v[c] == 3) && p.N == 512);
         const bool avail_r = cand_r[c] == 0 || p.N == 1024 || (cand_r[c] == 2 && p.N == 512);
         use[c] = (force_e == 0 || force_e == cand_e[c]) && (force_v < 0 || force_v == cand_v[c]) &&
                  (force_r < 0 || force_r == cand_r[c]) && avail_v && avail_r;
@@ -416,8 +416,9 @@ ts_status autotune(Plan& p)
 
 // Second autotuner stage: how many field groups to propagate concurrently (1, 2 or 4 streams), timed
 // as runs of four column + row pass pairs of B_t workspace fields per fork (the reported cost is per
-// pair).  Then, when that is two or more groups at N = 1024 with a prefetching column variant (8- or
-// 4-column tiles), both column variants are timed again the same way with that many groups: on one
+// pair).  Then, when that is two or more groups at N = 512 or 1024 with a prefetching column variant
+// (wide or narrow tiles: 16 / 8 columns at N = 512, 8 / 4 at 1024), both column variants are timed
+// again the same way with that many groups: on one
 // stream the two come within a few per cent of each other (so the first stage's pick between them
 // follows noise), while under concurrent groups they differ, so the column variant is taken from
 // this timing (the other one replaces the first stage's pick only when at least 1 % faster).  Cached
@@ -426,7 +427,7 @@ ts_status autotune(Plan& p)
 struct GroupChoice {
     int groups;
     int col_variant;  // -1: the first stage's pick stands
-    float us_cols[2];  // cost per pass pair of 8- / 4-column tiles with `groups` groups (0: not timed)
+    float us_cols[2];  // cost per pass pair of column variant 2 / 3 with `groups` groups (0: not timed)
 };
 std::map<std::tuple<int, int, int, int, int>, GroupChoice> g_group_cache;
 constexpr int kTuneSteps = 4;  // column + row pass pairs per fork in the group timing
@@ -518,7 +519,7 @@ ts_status autotune_groups(Plan& p)
     p.prop_groups = best_g;
     // the column tiles under the chosen concurrency
     GroupChoice gc{best_g, -1, {0.0f, 0.0f}};
-    const bool retime = e == cudaSuccess && best_g >= 2 && p.N == 1024 && p.fft_e == 32 && !p.split_bf16 &&
+    const bool retime = e == cudaSuccess && best_g >= 2 && (p.N == 1024 || p.N == 512) && p.fft_e == 32 && !p.split_bf16 &&
                         (p.col_variant == 2 || p.col_variant == 3) && std::getenv("TS_COL_VARIANT") == nullptr;
     if (retime) {
         const int first = p.col_variant;
@@ -882,13 +883,13 @@ ts_status ts_plan_tuning_candidates(ts_plan plan, int max, int* n, int* points_p
     return TS_OK;
 }
 
-ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_8_columns, float* us_4_columns)
+ts_status ts_plan_tuning_columns(ts_plan plan, int* col_variant, float* us_variant2, float* us_variant3)
 {
     if (!plan || !col_variant) return fail(TS_ERR_INVALID_ARG, "ts_plan_tuning_columns: need plan and output");
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     *col_variant = p->col_variant;
-    if (us_8_columns) *us_8_columns = p->tune_col_us[0];
-    if (us_4_columns) *us_4_columns = p->tune_col_us[1];
+    if (us_variant2) *us_variant2 = p->tune_col_us[0];
+    if (us_variant3) *us_variant3 = p->tune_col_us[1];
     return TS_OK;
 }
 

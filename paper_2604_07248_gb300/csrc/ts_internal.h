@@ -48,7 +48,8 @@ struct Plan {
     bool test_stall = false;   // TS_PLAN_TEST_STALL: prefetching passes skip their first copy
     int tc_col_groups = 1;     // tensor-core column tiles: 1 = 4 columns (4 CTAs / SM), 2 = 8 columns (2 CTAs / SM)
     int col_variant = 0;       // column pass: 0 = lines shared by warps, 1 = one warp per column, 2 / 3 =
-                               // persistent CTAs with TMA-prefetched 8- / 4-column tiles (1-3: N = 1024, E = 32)
+                               // persistent CTAs with TMA-prefetched wide / narrow tiles (N = 1024: 8 / 4
+                               // columns, N = 512: 16 / 8; variant 1 at N = 1024 only; E = 32)
     int row_variant = 0;       // row pass: 0 = per-CTA screen rows, 1 = phasor rows shared by the CTA's fields,
                                // 2 = persistent warps with bulk-copy prefetch of rows and phasor rows
     float tune_us[8] = {};     // autotuner timings of one column + row pass per candidate (kCandE/Col/Row)
@@ -58,7 +59,7 @@ struct Plan {
     float4* ht_all = nullptr;  // [S][N] (P_s, ky^2) for the fused launch (N = 1024)
     int* fused_ctr = nullptr;  // [(2S+1) max_batch + 1] completion counters and work counter of the fused launch
     float tune_group_us[3] = {0, 0, 0};  // autotuner timings for 1, 2, 4 groups
-    float tune_col_us[2] = {0, 0};       // 8- / 4-column tiles re-timed under the chosen field groups (0: not)
+    float tune_col_us[2] = {0, 0};       // column variants 2 / 3 re-timed under the chosen field groups (0: not)
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // extra streams for the field groups
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     float2* P = nullptr;       // [S][N] exp(-i dz kappa^2 / 2k) / N (or the separable form, see sep_transfer)

@@ -563,7 +563,7 @@ cudaError_t col_pass_n(int E, int variant, bool conj, bool sep, const ColParams&
 {
     if constexpr (N == 512 || N == 1024) {
         if ((variant == 2 || variant == 3) && E == 32) {
-            const int w = N == 512 ? 16 : (variant == 2 ? 8 : 4);
+            const int w = N == 512 ? (variant == 2 ? 16 : 8) : (variant == 2 ? 8 : 4);
             const int hmode = sep ? (cp.first_order_cross ? 3 : cp.tiny_cross ? 2 : 1) : 0;
             cudaError_t e = col_pass_tma(N, w, conj, hmode, cp, B, st, source);
             if (e != cudaErrorNotSupported || source) return e;

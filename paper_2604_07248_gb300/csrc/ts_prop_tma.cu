@@ -57,7 +57,10 @@ __device__ __forceinline__ void stage0_exchange_x4(float2 (&v)[32], float2* line
 // ---------------------------------------------------------------------------------------------
 // W columns per CTA (T W threads): N = 1024, W = 8, two CTAs per SM, the (P, ky^2) table as float4;
 // or W = 4, four CTAs per SM (block barriers span 4 warps instead of 8), the table split into P
-// (float2) and ky^2 (float) so that four CTAs fit the SM's shared memory; N = 512, W = 16, two per SM.
+// (float2) and ky^2 (float) so that four CTAs fit the SM's shared memory; N = 512, W = 16, two per SM,
+// or W = 8, four per SM (split table).  At N = 512 the line stride is the padded line (528 float2)
+// plus 16 / W (529 for W = 16, 530 for W = 8), which keeps the exchanges and the tile accesses of a
+// warp at the 2-wavefront minimum for 8-byte accesses.
 template <int N_, int W_>
 struct ColTma {
     static constexpr int N = N_, W = W_;
@@ -436,6 +439,7 @@ cudaError_t col_pass_tma(int N, int w, bool conj, int hmode, const ColParams& cp
     if (N == 1024 && w == 8) return col_dispatch_tma<ColTma<1024, 8>>(conj, hmode, cp, B, st, source);
     if (N == 1024 && w == 4) return col_dispatch_tma<ColTma<1024, 4>>(conj, hmode, cp, B, st, source);
     if (N == 512 && w == 16) return col_dispatch_tma<ColTma<512, 16>>(conj, hmode, cp, B, st, source);
+    if (N == 512 && w == 8) return col_dispatch_tma<ColTma<512, 8>>(conj, hmode, cp, B, st, source);
     return cudaErrorNotSupported;
 }
 
@@ -486,6 +490,7 @@ cudaError_t prepare_prop_tma(int N)
         row_attrs<RowTma<1024>>(e);
     } else if (N == 512) {
         col_attrs<ColTma<512, 16>>(e);
+        col_attrs<ColTma<512, 8>>(e);
         row_attrs<RowTma<512>>(e);
     }
     return e;

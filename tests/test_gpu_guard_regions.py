@@ -81,7 +81,7 @@ def _phasors(plan, N, S, seed=7):
 
 
 @pytest.mark.parametrize("N,dx,colv,fused", [(1024, 5e-4, 2, 0), (1024, 5e-4, 3, 0), (1024, 5e-4, 2, 1),
-                                             (512, 1e-3, 2, 0), (256, 1e-3, 0, 0)])
+                                             (512, 1e-3, 2, 0), (512, 1e-3, 3, 0), (256, 1e-3, 0, 0)])
 def test_propagation_writes_stay_inside_their_buffers(N, dx, colv, fused, monkeypatch):
     if N >= 512:
         _env(monkeypatch, TS_FFT_E=32, TS_COL_VARIANT=colv, TS_ROW_VARIANT=2, TS_PROP_STREAMS=1, TS_FUSED=fused)

@@ -460,11 +460,12 @@ def test_prefetching_passes_match_oracle(B, phi_group, colv, monkeypatch):
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
-@pytest.mark.parametrize("B,phi_group", [(4, 2), (3, 3), (1, 1)])
-def test_prefetching_passes_at_512_match_oracle(B, phi_group, monkeypatch):
-    # N = 512: 16-column tiles of 64 KiB, two rows per warp in the row pass (16 threads per row)
+@pytest.mark.parametrize("B,phi_group,colv", [(4, 2, 2), (3, 3, 2), (1, 1, 2), (4, 2, 3), (3, 3, 3), (1, 1, 3)])
+def test_prefetching_passes_at_512_match_oracle(B, phi_group, colv, monkeypatch):
+    # N = 512: 16-column tiles of 64 KiB (column variant 2, two CTAs per SM) or 8-column tiles of 32 KiB
+    # (variant 3, four per SM), two rows per warp in the row pass (16 threads per row)
     monkeypatch.setenv("TS_FFT_E", "32")
-    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_COL_VARIANT", str(colv))
     monkeypatch.setenv("TS_ROW_VARIANT", "2")
     monkeypatch.setenv("TS_PROP_STREAMS", "1")
     N, dx, S = 512, 1e-3, 3
@@ -472,7 +473,7 @@ def test_prefetching_passes_at_512_match_oracle(B, phi_group, monkeypatch):
     md = omedium(N, dx)
     plan = ts.Plan(LAM, N, dx, [100.0] * S, [1e-14] * S, l0=5e-3, L0=10.0, max_batch=B)
     tune = plan.tuning()
-    assert tune[0] == 32 and tune[5] == 2 and tune[7] == 2
+    assert tune[0] == 32 and tune[5] == colv and tune[7] == 2
     phis = np.stack([np.stack([O.make_screen(md, 1e-14, 100.0, 0, 70, s, g) for s in range(S)]) for g in range(G)])
     ph = torch.from_numpy(np.exp(1j * phis).astype(np.complex64)).to(DEV)
     rng = np.random.default_rng(71)
@@ -491,13 +492,14 @@ def test_prefetching_passes_at_512_match_oracle(B, phi_group, monkeypatch):
         assert rel_l2(gg[b], back) < TOL, (b, rel_l2(gg[b], back))
 
 
-@pytest.mark.parametrize("N,dx,groups", [(1024, 5e-4, 1), (1024, 5e-4, 2), (512, 1e-3, 2)])
-def test_sources_generated_in_the_first_column_pass(N, dx, groups, monkeypatch):
+@pytest.mark.parametrize("N,dx,groups,colv", [(1024, 5e-4, 1, 2), (1024, 5e-4, 2, 2), (512, 1e-3, 2, 2),
+                                              (512, 1e-3, 2, 3)])
+def test_sources_generated_in_the_first_column_pass(N, dx, groups, colv, monkeypatch):
     # with TS_PROP_SOURCE and the prefetching column pass, the first row pass is skipped: the column
     # pass builds the row transform of each source (Gaussians and a plane wave, cycling over 3
     # sources; with two concurrent field groups the second starts at source 2) from an FP64 table
     monkeypatch.setenv("TS_FFT_E", "32")
-    monkeypatch.setenv("TS_COL_VARIANT", "2")
+    monkeypatch.setenv("TS_COL_VARIANT", str(colv))
     monkeypatch.setenv("TS_ROW_VARIANT", "2")
     monkeypatch.setenv("TS_PROP_STREAMS", str(groups))
     monkeypatch.setenv("TS_FUSED", "0")
